@@ -1,0 +1,264 @@
+"""Plain FP64 CPU oracle of the MHD + GLM residual (arXiv 2209.04481).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+``bench.py``'s CPU-baseline / reference arm may import this package.  It shares
+no code with ``paper_2209_04481_gb300`` (the CUDA library) and imports nothing
+from it; both follow the same definitions, written out independently.
+
+The arithmetic lives in ``corona_oracle.cpp`` (plain scalar C++ loops, face by
+face, compiled with ``-ffp-contract=off``); this module compiles it with g++
+on first use and marshals numpy arrays through ctypes.
+
+Array layout: conservative state ``U`` of shape ``(9, n0, n1, n2)`` float64,
+variables (rho, rho Vx, rho Vy, rho Vz, Bx, By, Bz, E, psi); for the spherical
+shell the axes are (r, theta, phi), phi fastest.  ``Br`` has shape
+``(n_theta, n_phi)``: the prescribed radial field at the inner face centres.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "corona_oracle.cpp")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+GEOM_SPHERE, GEOM_BOX = 0, 1
+BC_PERIODIC, BC_COPY = 0, 1
+LIMITERS = {"none": 0, "minmod": 1, "vanalbada": 2}
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/_build/liboracle.so`` (g++, -O2, no FP contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math",
+           "-fPIC", "-shared", "-o", tmp, _SRC]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Desc(ctypes.Structure):
+    _fields_ = [
+        ("geom", ctypes.c_int32),
+        ("n0", ctypes.c_int32), ("n1", ctypes.c_int32), ("n2", ctypes.c_int32),
+        ("r_in", ctypes.c_double), ("r_out", ctypes.c_double),
+        ("len0", ctypes.c_double), ("len1", ctypes.c_double), ("len2", ctypes.c_double),
+        ("bc0", ctypes.c_int32), ("bc1", ctypes.c_int32), ("bc2", ctypes.c_int32),
+        ("limiter", ctypes.c_int32),
+        ("lim_eps", ctypes.c_double),
+        ("gamma", ctypes.c_double), ("c_h", ctypes.c_double), ("g0", ctypes.c_double),
+        ("outer_rho_exp", ctypes.c_double), ("outer_br_exp", ctypes.c_double),
+        ("rho_b", ctypes.c_double), ("p_b", ctypes.c_double),
+    ]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.POINTER(ctypes.c_double)
+            D = ctypes.POINTER(_Desc)
+            lib.orc_residual.argtypes = [D, P, P, P, P, P, P, P]
+            lib.orc_residual_jvp.argtypes = [D, P, P, P, P, P, P]
+            lib.orc_flux.argtypes = [P, P, P, ctypes.c_double, ctypes.c_double, P, P]
+            lib.orc_cons_to_prim.argtypes = [D, P, P]
+            lib.orc_geometry.argtypes = [D, P, P, P, P]
+            lib.orc_ghosts.argtypes = [D, P, P, P, P]
+            lib.orc_pseudo_time_step.argtypes = [D, P, P, ctypes.c_int, ctypes.c_double, P, P]
+            for f in (lib.orc_residual, lib.orc_residual_jvp, lib.orc_flux, lib.orc_cons_to_prim,
+                      lib.orc_geometry, lib.orc_ghosts, lib.orc_pseudo_time_step):
+                f.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+@dataclass
+class Grid:
+    """Problem description: the spherical shell (default) or a Cartesian box.
+
+    Defaults are the solar-wind configuration: r in [1, 21.5] R_sun, gamma = 1.05,
+    c_h = 1 (Sect. 3.3), g0 = G M_sun / (R_sun V_ref^2) with V_ref the Alfven speed
+    of the Sect. 2.1 reference values, outer law of Table 2 case 3.
+    """
+    n_r: int = 32
+    n_theta: int = 16
+    n_phi: int = 32
+    r_in: float = 1.0
+    r_out: float = 21.5
+    gamma: float = 1.05
+    c_h: float = 1.0
+    g0: float = 0.0
+    limiter: str = "vanalbada"
+    lim_eps: float = 1e-12
+    outer_rho_exp: float = 2.0
+    outer_br_exp: float = 2.0
+    rho_b: float = 1.0
+    p_b: float = 0.0
+    geom: int = GEOM_SPHERE
+    lengths: tuple = (1.0, 1.0, 1.0)
+    bcs: tuple = (BC_PERIODIC, BC_PERIODIC, BC_PERIODIC)
+    _desc: _Desc = field(default=None, init=False, repr=False)
+
+    @property
+    def shape(self):
+        return (self.n_r, self.n_theta, self.n_phi)
+
+    @property
+    def ncell(self):
+        return self.n_r * self.n_theta * self.n_phi
+
+    def desc(self) -> _Desc:
+        d = _Desc()
+        d.geom = self.geom
+        d.n0, d.n1, d.n2 = self.n_r, self.n_theta, self.n_phi
+        d.r_in, d.r_out = self.r_in, self.r_out
+        d.len0, d.len1, d.len2 = self.lengths
+        d.bc0, d.bc1, d.bc2 = self.bcs
+        d.limiter = LIMITERS[self.limiter]
+        d.lim_eps = self.lim_eps
+        d.gamma, d.c_h, d.g0 = self.gamma, self.c_h, self.g0
+        d.outer_rho_exp, d.outer_br_exp = self.outer_rho_exp, self.outer_br_exp
+        d.rho_b, d.p_b = self.rho_b, self.p_b
+        return d
+
+
+def box(nx, ny, nz, lengths=(1.0, 1.0, 1.0), bcs=(BC_PERIODIC,) * 3, **kw) -> Grid:
+    """Cartesian box grid (axis 0 = x slowest, axis 2 = z fastest); no gravity."""
+    return Grid(n_r=nx, n_theta=ny, n_phi=nz, geom=GEOM_BOX, lengths=tuple(lengths),
+                bcs=tuple(bcs), g0=0.0, **kw)
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None and a.shape != tuple(shape):
+        a = a.reshape(shape)
+    return a
+
+
+def residual(grid: Grid, U, Br=None, want_scale=False, want_bflux=False):
+    """Residual R = dU/dt of shape (9, n0, n1, n2), per-variable L2 norms and dtmin.
+
+    Returns a dict with keys ``R``, ``norms`` (9,), ``dtmin`` and optionally
+    ``scale`` (flux-magnitude scale, same shape as R) and ``bflux`` ((2, 9): the
+    sum of F*|S| over the inner and the outer boundary faces).
+    """
+    lib = _load()
+    U = _f64(U, (9,) + grid.shape)
+    if grid.geom == GEOM_SPHERE:
+        Br = _f64(Br, (grid.n_theta, grid.n_phi))
+    R = np.empty_like(U)
+    norms = np.empty(9)
+    dtmin = np.empty(1)
+    scale = np.empty_like(U) if want_scale else None
+    bflux = np.empty(18) if want_bflux else None
+    d = grid.desc()
+    rc = lib.orc_residual(ctypes.byref(d), _ptr(U), _ptr(Br), _ptr(R), _ptr(norms),
+                          _ptr(dtmin), _ptr(scale), _ptr(bflux))
+    if rc:
+        raise ValueError("oracle rejected the problem description")
+    out = {"R": R, "norms": norms, "dtmin": float(dtmin[0])}
+    if want_scale:
+        out["scale"] = scale
+    if want_bflux:
+        out["bflux"] = bflux.reshape(2, 9)
+    return out
+
+
+def residual_jvp(grid: Grid, U, Br, dU, dBr):
+    """(R, dR) with dR = dR/dU . dU + dR/dBr . dBr (forward-mode dual numbers)."""
+    lib = _load()
+    U = _f64(U, (9,) + grid.shape)
+    dU = _f64(dU, (9,) + grid.shape)
+    if grid.geom == GEOM_SPHERE:
+        Br = _f64(Br, (grid.n_theta, grid.n_phi))
+        dBr = _f64(dBr, (grid.n_theta, grid.n_phi))
+    R = np.empty_like(U)
+    dR = np.empty_like(U)
+    d = grid.desc()
+    rc = lib.orc_residual_jvp(ctypes.byref(d), _ptr(U), _ptr(Br), _ptr(dU), _ptr(dBr),
+                              _ptr(R), _ptr(dR))
+    if rc:
+        raise ValueError("oracle rejected the problem description")
+    return R, dR
+
+
+def flux(wl, wr, n, gamma=1.05, c_h=1.0):
+    """Rusanov + GLM flux through unit normal n for primitive states; returns (F, lambda)."""
+    lib = _load()
+    wl, wr, n = _f64(wl), _f64(wr), _f64(n)
+    F = np.empty(9)
+    lam = np.empty(1)
+    lib.orc_flux(_ptr(wl), _ptr(wr), _ptr(n), gamma, c_h, _ptr(F), _ptr(lam))
+    return F, float(lam[0])
+
+
+def cons_to_prim(grid: Grid, U):
+    lib = _load()
+    U = _f64(U, (9,) + grid.shape)
+    W = np.empty_like(U)
+    d = grid.desc()
+    if lib.orc_cons_to_prim(ctypes.byref(d), _ptr(U), _ptr(W)):
+        raise ValueError("bad description")
+    return W
+
+
+def geometry(grid: Grid):
+    """Cell volumes and face-area vectors of the three face families."""
+    lib = _load()
+    n0, n1, n2 = grid.shape
+    vol = np.empty((n0, n1, n2))
+    S0 = np.empty((n0 + 1, n1, n2, 3))
+    S1 = np.empty((n0, n1 + 1, n2, 3))
+    S2 = np.empty((n0, n1, n2 + 1, 3))
+    d = grid.desc()
+    if lib.orc_geometry(ctypes.byref(d), _ptr(vol), _ptr(S0), _ptr(S1), _ptr(S2)):
+        raise ValueError("bad description")
+    return vol, S0, S1, S2
+
+
+def ghosts(grid: Grid, U, Br):
+    """Primitive ghost planes (inner, outer), each of shape (9, n_theta, n_phi)."""
+    lib = _load()
+    U = _f64(U, (9,) + grid.shape)
+    Br = _f64(Br, (grid.n_theta, grid.n_phi))
+    Win = np.empty((9, grid.n_theta, grid.n_phi))
+    Wout = np.empty_like(Win)
+    d = grid.desc()
+    if lib.orc_ghosts(ctypes.byref(d), _ptr(U), _ptr(Br), _ptr(Win), _ptr(Wout)):
+        raise ValueError("bad description")
+    return Win, Wout
+
+
+def pseudo_time_step(grid: Grid, U, Br, nsteps: int, cfl: float):
+    """Explicit pseudo-time steps; returns (U_new, res_log10 (nsteps, 9), dt (nsteps,))."""
+    lib = _load()
+    U = _f64(U, (9,) + grid.shape).copy()
+    if grid.geom == GEOM_SPHERE:
+        Br = _f64(Br, (grid.n_theta, grid.n_phi))
+    res = np.empty((max(nsteps, 1), 9))
+    dts = np.empty(max(nsteps, 1))
+    d = grid.desc()
+    if lib.orc_pseudo_time_step(ctypes.byref(d), _ptr(U), _ptr(Br), int(nsteps), float(cfl),
+                                _ptr(res), _ptr(dts)):
+        raise ValueError("bad description")
+    return U, res[:nsteps], dts[:nsteps]

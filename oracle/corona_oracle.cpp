@@ -1,0 +1,715 @@
+// corona_oracle.cpp -- plain, slow FP64 CPU oracle of the finite-volume
+// ideal-MHD + GLM residual of arXiv 2209.04481.
+//
+// TEST INFRASTRUCTURE ONLY.  This file is the checker, not the product: only
+// the test-suite, the smoke check and the benchmark's CPU-baseline / reference
+// arm may load it.  It shares no source, header, table or helper with the CUDA
+// library; both are written independently from the same definitions.
+//
+// What it computes (paper sections in brackets):
+//   * conservative state U = (rho, rho V, B, E, psi), primitive state
+//     W = (rho, V, B, p, psi), E = p/(gamma-1) + rho V^2/2 + B^2/2
+//     [Sect. 2.2, ideal-MHD system; Alfven-speed units absorb the 4 pi of the
+//     printed Gaussian form, Sect. 2.1 reference values];
+//   * exact face-area vectors and volumes of a (r, theta, phi) shell
+//     (structured stand-in for the prism mesh of Sect. 2.1);
+//   * ghost states: the "low-E" inner boundary V_b x B_b = 0 with B_r
+//     prescribed and B_theta, B_phi Neumann [Sect. 3.2], psi_b = 0
+//     [Sect. 3.3]; the outer extrapolation laws of Table 2 (case 3 by
+//     default: rho, p ~ r^-a, B_r ~ r^-2, psi_b = 0) [Sect. 4.1];
+//     across-pole theta ghosts and periodic phi;
+//   * limited linear reconstruction (second-order FV, Sect. 2.1);
+//   * Rusanov flux with the GLM divergence-cleaning pair (psi, c_h)
+//     [Sect. 2.1 "hyperbolic divergence cleaning", Sect. 3.3 c_h = 1];
+//   * residual R = dU/dt = -(1/V) sum_f F*.S + S_grav  [Sect. 2.2 sources];
+//   * residual norms, local pseudo-time step bound, explicit pseudo-time
+//     stepping and the res(a) monitor of Sect. 2.1 (log10 of the L2 norm of
+//     a^t - a^{t+1});
+//   * a forward-mode (dual number) Jacobian-vector product of the residual.
+//
+// Readings where the paper is silent are the same as the CUDA library's and
+// are listed in the design notes: Rusanov + GLM-Dedner mixed form without
+// damping, van Albada limiter (smooth form, eps = 1e-12) / minmod / none,
+// V_b = projection of the interior V on B_b, rho_g = rho_b and p_g = p_b at
+// the inner ghost, mirror ghosts (face mean equals the boundary value).
+//
+// Compiled with -O2 -ffp-contract=off: every operation is a plain IEEE op.
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// forward-mode dual number: value and one tangent
+// ---------------------------------------------------------------------------
+struct Dual {
+  double v, d;
+  Dual(double v_ = 0.0, double d_ = 0.0) : v(v_), d(d_) {}
+};
+inline Dual operator+(Dual a, Dual b) { return Dual(a.v + b.v, a.d + b.d); }
+inline Dual operator-(Dual a, Dual b) { return Dual(a.v - b.v, a.d - b.d); }
+inline Dual operator-(Dual a) { return Dual(-a.v, -a.d); }
+inline Dual operator*(Dual a, Dual b) { return Dual(a.v * b.v, a.d * b.v + a.v * b.d); }
+inline Dual operator/(Dual a, Dual b) {
+  double q = a.v / b.v;
+  return Dual(q, (a.d - q * b.d) / b.v);
+}
+inline Dual& operator+=(Dual& a, Dual b) { a = a + b; return a; }
+inline Dual& operator-=(Dual& a, Dual b) { a = a - b; return a; }
+inline Dual sqrt(Dual a) {
+  double s = std::sqrt(a.v);
+  return Dual(s, a.d / (2.0 * s));
+}
+
+inline double val(double a) { return a; }
+inline double val(const Dual& a) { return a.v; }
+inline double tan_of(double) { return 0.0; }
+inline double tan_of(const Dual& a) { return a.d; }
+
+// |x| with d|x|/dx = +1 at x = 0
+inline double vabs(double a) { return a >= 0.0 ? a : -a; }
+inline Dual vabs(Dual a) { return a.v >= 0.0 ? a : -a; }
+// max(a, b); at a tie the first argument wins (also for the tangent)
+template <class T> inline T vmax(T a, T b) { return val(b) > val(a) ? b : a; }
+inline double vsqrt(double a) { return std::sqrt(a); }
+inline Dual vsqrt(Dual a) { return sqrt(a); }
+
+// ---------------------------------------------------------------------------
+// problem description (mirrors orc_desc below)
+// ---------------------------------------------------------------------------
+enum { GEOM_SPHERE = 0, GEOM_BOX = 1 };
+enum { BC_PERIODIC = 0, BC_COPY = 1 };
+enum { LIM_NONE = 0, LIM_MINMOD = 1, LIM_VANALBADA = 2 };
+
+// primitive indices
+enum { W_RHO = 0, W_VX, W_VY, W_VZ, W_BX, W_BY, W_BZ, W_P, W_PSI };
+// conservative indices
+enum { U_RHO = 0, U_MX, U_MY, U_MZ, U_BX, U_BY, U_BZ, U_E, U_PSI };
+
+}  // namespace
+
+extern "C" {
+typedef struct {
+  int32_t geom;            // 0 spherical shell, 1 Cartesian box
+  int32_t n0, n1, n2;      // cells along axis 0 (r | x), 1 (theta | y), 2 (phi | z)
+  double r_in, r_out;      // shell radii (sphere)
+  double len0, len1, len2; // box edge lengths (box)
+  int32_t bc0, bc1, bc2;   // box boundary kind per axis: 0 periodic, 1 zero-gradient
+  int32_t limiter;         // 0 none, 1 minmod, 2 van Albada
+  double lim_eps;          // van Albada epsilon
+  double gamma, c_h, g0;   // ratio of specific heats, cleaning speed, gravity
+  double outer_rho_exp;    // outer ghost: rho, p scaled by (r_I/r_G)^a
+  double outer_br_exp;     // outer ghost: B_r scaled by (r_I/r_G)^b
+  double rho_b, p_b;       // inner boundary density and pressure
+} orc_desc;
+}
+
+namespace {
+
+const double PI = 3.14159265358979323846;
+
+// ---------------------------------------------------------------------------
+// state conversions [Sect. 2.2: E = rho e + rho V^2/2 + B^2/2, rho e = p/(gamma-1)]
+// ---------------------------------------------------------------------------
+template <class T>
+void cons_to_prim(const T u[9], double gamma, T w[9]) {
+  T rho = u[U_RHO];
+  T vx = u[U_MX] / rho, vy = u[U_MY] / rho, vz = u[U_MZ] / rho;
+  T kin = 0.5 * rho * (vx * vx + vy * vy + vz * vz);
+  T mag = 0.5 * (u[U_BX] * u[U_BX] + u[U_BY] * u[U_BY] + u[U_BZ] * u[U_BZ]);
+  w[W_RHO] = rho;
+  w[W_VX] = vx; w[W_VY] = vy; w[W_VZ] = vz;
+  w[W_BX] = u[U_BX]; w[W_BY] = u[U_BY]; w[W_BZ] = u[U_BZ];
+  w[W_P] = (gamma - 1.0) * (u[U_E] - kin - mag);
+  w[W_PSI] = u[U_PSI];
+}
+
+template <class T>
+void prim_to_cons(const T w[9], double gamma, T u[9]) {
+  T rho = w[W_RHO];
+  T v2 = w[W_VX] * w[W_VX] + w[W_VY] * w[W_VY] + w[W_VZ] * w[W_VZ];
+  T b2 = w[W_BX] * w[W_BX] + w[W_BY] * w[W_BY] + w[W_BZ] * w[W_BZ];
+  u[U_RHO] = rho;
+  u[U_MX] = rho * w[W_VX]; u[U_MY] = rho * w[W_VY]; u[U_MZ] = rho * w[W_VZ];
+  u[U_BX] = w[W_BX]; u[U_BY] = w[W_BY]; u[U_BZ] = w[W_BZ];
+  u[U_E] = w[W_P] / (gamma - 1.0) + 0.5 * rho * v2 + 0.5 * b2;
+  u[U_PSI] = w[W_PSI];
+}
+
+// ---------------------------------------------------------------------------
+// physical flux through a unit normal n and the fast magnetosonic speed
+// [Sect. 2.2 flux vectors; GLM pair: F_B += psi n, F_psi = c_h^2 B_n]
+// ---------------------------------------------------------------------------
+template <class T>
+void physical_flux(const T w[9], const double n[3], double gamma, double ch,
+                   T f[9], T u[9], T& speed) {
+  T rho = w[W_RHO];
+  T vx = w[W_VX], vy = w[W_VY], vz = w[W_VZ];
+  T bx = w[W_BX], by = w[W_BY], bz = w[W_BZ];
+  T p = w[W_P], psi = w[W_PSI];
+  T un = vx * n[0] + vy * n[1] + vz * n[2];
+  T bn = bx * n[0] + by * n[1] + bz * n[2];
+  T b2 = bx * bx + by * by + bz * bz;
+  T vb = vx * bx + vy * by + vz * bz;
+  T pt = p + 0.5 * b2;
+  prim_to_cons(w, gamma, u);
+  T en = u[U_E];
+  f[U_RHO] = rho * un;
+  f[U_MX] = rho * vx * un + pt * n[0] - bx * bn;
+  f[U_MY] = rho * vy * un + pt * n[1] - by * bn;
+  f[U_MZ] = rho * vz * un + pt * n[2] - bz * bn;
+  f[U_BX] = un * bx - bn * vx + psi * n[0];
+  f[U_BY] = un * by - bn * vy + psi * n[1];
+  f[U_BZ] = un * bz - bn * vz + psi * n[2];
+  f[U_E] = (en + pt) * un - bn * vb;
+  f[U_PSI] = (ch * ch) * bn;
+  // fast speed: c_f^2 = ((a^2+b^2) + sqrt((a^2+b^2)^2 - 4 a^2 B_n^2/rho)) / 2
+  T a2 = gamma * p / rho;
+  T ba2 = b2 / rho;
+  T s = a2 + ba2;
+  T disc = s * s - 4.0 * a2 * bn * bn / rho;
+  if (val(disc) < 0.0) disc = T(0.0);
+  T cf = vsqrt(0.5 * (s + vsqrt(disc)));
+  speed = vabs(un) + cf;
+}
+
+// Rusanov (local Lax-Friedrichs) flux: F* = (F_L + F_R)/2 - lambda (U_R - U_L)/2
+// with lambda = max(|u_n|+c_f left, right, c_h).
+template <class T>
+void rusanov_flux(const T wl[9], const T wr[9], const double n[3], double gamma,
+                  double ch, T f[9], T& lam) {
+  T fl[9], fr[9], ul[9], ur[9], sl, sr;
+  physical_flux(wl, n, gamma, ch, fl, ul, sl);
+  physical_flux(wr, n, gamma, ch, fr, ur, sr);
+  lam = vmax(vmax(sl, sr), T(ch));
+  for (int v = 0; v < 9; ++v) f[v] = 0.5 * (fl[v] + fr[v]) - 0.5 * lam * (ur[v] - ul[v]);
+}
+
+// slope limiter on two one-sided slopes
+template <class T>
+T limited_slope(T a, T b, int limiter, double eps) {
+  if (limiter == LIM_NONE) return 0.5 * (a + b);
+  if (limiter == LIM_MINMOD) {
+    if (val(a) * val(b) <= 0.0) return T(0.0);
+    return val(vabs(a)) < val(vabs(b)) ? a : b;
+  }
+  // van Albada (smooth form)
+  return (a * (b * b + eps) + b * (a * a + eps)) / (a * a + b * b + 2.0 * eps);
+}
+
+// ---------------------------------------------------------------------------
+// the mesh
+// ---------------------------------------------------------------------------
+struct Mesh {
+  orc_desc d;
+  int n[3];
+  long ncell;
+  std::vector<double> rf;  // sphere radial faces, n0+1
+
+  explicit Mesh(const orc_desc& dd) : d(dd) {
+    n[0] = d.n0; n[1] = d.n1; n[2] = d.n2;
+    ncell = (long)n[0] * n[1] * n[2];
+    if (d.geom == GEOM_SPHERE) {
+      rf.resize(n[0] + 1);
+      // geometric radial stretch: r_k = r_in (r_out/r_in)^(k/N_r)
+      for (int k = 0; k <= n[0]; ++k)
+        rf[k] = d.r_in * std::pow(d.r_out / d.r_in, double(k) / n[0]);
+      rf[0] = d.r_in;
+      rf[n[0]] = d.r_out;
+    }
+  }
+  long idx(int a, int b, int c) const { return ((long)a * n[1] + b) * n[2] + c; }
+
+  // sphere coordinates
+  double rc(int k) const {  // cell-centre radius, with mirrored ghost centres
+    if (k < 0) return 2.0 * d.r_in - rc(0);
+    if (k >= n[0]) return 2.0 * d.r_out - rc(n[0] - 1);
+    return 0.5 * (rf[k] + rf[k + 1]);
+  }
+  double tface(int j) const { return PI * j / n[1]; }
+  double pface(int i) const { return 2.0 * PI * i / n[2]; }
+  double tc(int j) const { return 0.5 * (tface(j) + tface(j + 1)); }
+  double pc(int i) const { return 0.5 * (pface(i) + pface(i + 1)); }
+  void rhat(int j, int i, double e[3]) const {
+    double t = tc(j), p = pc(i);
+    e[0] = std::sin(t) * std::cos(p);
+    e[1] = std::sin(t) * std::sin(p);
+    e[2] = std::cos(t);
+  }
+
+  double h(int ax) const {  // box spacing
+    double L = ax == 0 ? d.len0 : (ax == 1 ? d.len1 : d.len2);
+    return L / n[ax];
+  }
+
+  // cell volume
+  double volume(int a, int b, int c) const {
+    if (d.geom == GEOM_BOX) return h(0) * h(1) * h(2);
+    (void)c;
+    double r1 = rf[a], r2 = rf[a + 1];
+    double t1 = tface(b), t2 = tface(b + 1);
+    double dp = 2.0 * PI / n[2];
+    return (r2 * r2 * r2 - r1 * r1 * r1) / 3.0 * (std::cos(t1) - std::cos(t2)) * dp;
+  }
+
+  // exact face-area vector S = integral of the unit normal over the face, for
+  // the face of axis `ax` at face index `f` along that axis, with the other two
+  // cell indices given.  The normal points towards increasing coordinate.
+  void face_vector(int ax, int f, int o1, int o2, double S[3]) const {
+    if (d.geom == GEOM_BOX) {
+      S[0] = S[1] = S[2] = 0.0;
+      S[ax] = (ax == 0 ? h(1) * h(2) : (ax == 1 ? h(0) * h(2) : h(0) * h(1)));
+      return;
+    }
+    if (ax == 0) {  // r-face at rf[f], cell column (j = o1, i = o2)
+      double r = rf[f];
+      double t1 = tface(o1), t2 = tface(o1 + 1);
+      double p1 = pface(o2), p2 = pface(o2 + 1);
+      double X = 0.5 * ((t2 - std::sin(t2) * std::cos(t2)) - (t1 - std::sin(t1) * std::cos(t1)));
+      double Z = 0.5 * (std::sin(t2) * std::sin(t2) - std::sin(t1) * std::sin(t1));
+      S[0] = r * r * X * (std::sin(p2) - std::sin(p1));
+      S[1] = r * r * X * (std::cos(p1) - std::cos(p2));
+      S[2] = r * r * Z * (p2 - p1);
+    } else if (ax == 1) {  // theta-face at tface(f), shell k = o1, column i = o2
+      if (f == 0 || f == n[1]) { S[0] = S[1] = S[2] = 0.0; return; }  // poles
+      double r1 = rf[o1], r2 = rf[o1 + 1];
+      double t = tface(f);
+      double p1 = pface(o2), p2 = pface(o2 + 1);
+      double a = 0.5 * (r2 * r2 - r1 * r1) * std::sin(t);
+      S[0] = a * std::cos(t) * (std::sin(p2) - std::sin(p1));
+      S[1] = a * std::cos(t) * (std::cos(p1) - std::cos(p2));
+      S[2] = -a * std::sin(t) * (p2 - p1);
+    } else {  // phi-face at pface(f), shell k = o1, row j = o2
+      double r1 = rf[o1], r2 = rf[o1 + 1];
+      double t1 = tface(o2), t2 = tface(o2 + 1);
+      double p = pface(f);
+      double a = 0.5 * (r2 * r2 - r1 * r1) * (t2 - t1);
+      S[0] = -a * std::sin(p);
+      S[1] = a * std::cos(p);
+      S[2] = 0.0;
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// ghost states
+// ---------------------------------------------------------------------------
+// Inner "low-E" ghost at r = r_in for column (j, i) from the interior
+// primitive state wi and the prescribed B_r [Sect. 3.2: V_b x B_b = 0 fixes the
+// direction of V_b; B_r from the magnetogram; B_theta, B_phi Neumann;
+// Sect. 3.3: psi_b = 0].  Ghost = 2 * boundary - interior (face mean equals the
+// boundary value) for B and V; rho, p Dirichlet at the ghost centre.
+template <class T>
+void inner_ghost(const Mesh& m, int j, int i, const T wi[9], T br, T wg[9]) {
+  double e[3];
+  m.rhat(j, i, e);
+  T bi[3] = {wi[W_BX], wi[W_BY], wi[W_BZ]};
+  T vi[3] = {wi[W_VX], wi[W_VY], wi[W_VZ]};
+  T bir = bi[0] * e[0] + bi[1] * e[1] + bi[2] * e[2];
+  T bb[3], vb[3];
+  for (int c = 0; c < 3; ++c) bb[c] = br * e[c] + (bi[c] - bir * e[c]);
+  T bb2 = bb[0] * bb[0] + bb[1] * bb[1] + bb[2] * bb[2];
+  T vdotb = vi[0] * bb[0] + vi[1] * bb[1] + vi[2] * bb[2];
+  T den = vmax(bb2, T(1e-300));
+  for (int c = 0; c < 3; ++c) vb[c] = vdotb * bb[c] / den;
+  wg[W_RHO] = T(m.d.rho_b);
+  wg[W_P] = T(m.d.p_b);
+  for (int c = 0; c < 3; ++c) {
+    wg[W_VX + c] = 2.0 * vb[c] - vi[c];
+    wg[W_BX + c] = 2.0 * bb[c] - bi[c];
+  }
+  wg[W_PSI] = -wi[W_PSI];
+}
+
+// Outer ghost at r = r_out [Sect. 4.1, Table 2 case 3 by default]:
+// rho_G = rho_I (r_I/r_G)^a, p likewise, B_r,G = B_r,I (r_I/r_G)^b with the
+// tangential B, and V, zero-gradient; psi_b = 0 (Dirichlet on the boundary).
+template <class T>
+void outer_ghost(const Mesh& m, int j, int i, const T wi[9], T wg[9]) {
+  double e[3];
+  m.rhat(j, i, e);
+  double rI = m.rc(m.n[0] - 1);
+  double rG = 2.0 * m.d.r_out - rI;
+  double fa = std::pow(rI / rG, m.d.outer_rho_exp);
+  double fb = std::pow(rI / rG, m.d.outer_br_exp);
+  T bir = wi[W_BX] * e[0] + wi[W_BY] * e[1] + wi[W_BZ] * e[2];
+  wg[W_RHO] = wi[W_RHO] * fa;
+  wg[W_P] = wi[W_P] * fa;
+  for (int c = 0; c < 3; ++c) {
+    wg[W_VX + c] = wi[W_VX + c];
+    wg[W_BX + c] = wi[W_BX + c] + (bir * fb - bir) * e[c];
+  }
+  wg[W_PSI] = -wi[W_PSI];
+}
+
+// ---------------------------------------------------------------------------
+// the residual
+// ---------------------------------------------------------------------------
+template <class T>
+struct State {
+  const Mesh& m;
+  std::vector<T> W;    // AoS primitives, 9 per cell
+  std::vector<T> Gin;  // inner ghost plane (sphere), 9 per (j, i)
+  std::vector<T> Gout; // outer ghost plane (sphere)
+
+  State(const Mesh& mm, const T* U, const T* Br) : m(mm) {
+    long N = m.ncell;
+    W.resize(9 * N);
+    for (long c = 0; c < N; ++c) {
+      T u[9];
+      for (int v = 0; v < 9; ++v) u[v] = U[v * N + c];
+      cons_to_prim(u, m.d.gamma, &W[9 * c]);
+    }
+    if (m.d.geom == GEOM_SPHERE) {
+      int nt = m.n[1], np = m.n[2], nr = m.n[0];
+      Gin.resize(9 * (long)nt * np);
+      Gout.resize(9 * (long)nt * np);
+      for (int j = 0; j < nt; ++j)
+        for (int i = 0; i < np; ++i) {
+          long col = (long)j * np + i;
+          inner_ghost(m, j, i, &W[9 * m.idx(0, j, i)], Br[col], &Gin[9 * col]);
+          outer_ghost(m, j, i, &W[9 * m.idx(nr - 1, j, i)], &Gout[9 * col]);
+        }
+    }
+  }
+
+  // primitive state at cell (a, b, c) where indices may step outside the
+  // domain by the one or two ghost layers the stencil needs.
+  const T* at(int a, int b, int c) const {
+    if (m.d.geom == GEOM_SPHERE) {
+      int nr = m.n[0], nt = m.n[1], np = m.n[2];
+      if (b < 0) { b = -1 - b; c += np / 2; }          // across the north pole
+      else if (b >= nt) { b = 2 * nt - 1 - b; c += np / 2; }  // south pole
+      c = ((c % np) + np) % np;                        // periodic phi
+      if (a < 0) return &Gin[9 * ((long)b * np + c)];
+      if (a >= nr) return &Gout[9 * ((long)b * np + c)];
+      return &W[9 * m.idx(a, b, c)];
+    }
+    int ix[3] = {a, b, c};
+    int bc[3] = {m.d.bc0, m.d.bc1, m.d.bc2};
+    for (int ax = 0; ax < 3; ++ax) {
+      int nn = m.n[ax];
+      if (bc[ax] == BC_PERIODIC) ix[ax] = ((ix[ax] % nn) + nn) % nn;
+      else ix[ax] = std::min(std::max(ix[ax], 0), nn - 1);  // zero-gradient ghost
+    }
+    return &W[9 * m.idx(ix[0], ix[1], ix[2])];
+  }
+};
+
+// distances used by the reconstruction along axis `ax` for cell index `a`
+// (possibly a ghost index): centre-to-centre distance to the lower (dm) and
+// upper (dp) neighbour, and centre-to-face offsets to the lower (hm) and upper
+// (hp) face.  Index units everywhere except the sphere's radial axis, which
+// uses physical radii.
+struct Spacing { double dm, dp, hm, hp; };
+Spacing spacing(const Mesh& m, int ax, int a) {
+  if (m.d.geom == GEOM_SPHERE && ax == 0) {
+    Spacing s;
+    s.dm = m.rc(a) - m.rc(a - 1);
+    s.dp = m.rc(a + 1) - m.rc(a);
+    s.hm = m.rc(a) - m.rf[a];
+    s.hp = m.rf[a + 1] - m.rc(a);
+    return s;
+  }
+  return Spacing{1.0, 1.0, 0.5, 0.5};
+}
+
+template <class T>
+struct Residual {
+  std::vector<T> R;         // 9 x N, variable-major
+  std::vector<double> lam;  // per cell: sum over faces of lambda |S|
+  std::vector<double> scale;// 9 x N: (1/V) sum_f |F*_v| |S|
+  T bin[9], bout[9];        // sum of F*|S| over inner / outer boundary faces
+};
+
+// the cell triple of the cell `a` steps along axis `ax` from (p0, p1, p2)
+inline void shift(int ax, int a, const int base[3], int out[3]) {
+  out[0] = base[0]; out[1] = base[1]; out[2] = base[2];
+  out[ax] = a;
+}
+
+template <class T>
+void residual_core(const Mesh& m, const T* U, const T* Br, Residual<T>& res) {
+  const long N = m.ncell;
+  const double gamma = m.d.gamma, ch = m.d.c_h;
+  State<T> st(m, U, Br);
+  res.R.assign(9 * N, T(0.0));
+  res.lam.assign(N, 0.0);
+  res.scale.assign(9 * N, 0.0);
+  for (int v = 0; v < 9; ++v) { res.bin[v] = T(0.0); res.bout[v] = T(0.0); }
+
+  bool periodic[3];
+  if (m.d.geom == GEOM_SPHERE) { periodic[0] = false; periodic[1] = false; periodic[2] = true; }
+  else { periodic[0] = m.d.bc0 == BC_PERIODIC; periodic[1] = m.d.bc1 == BC_PERIODIC; periodic[2] = m.d.bc2 == BC_PERIODIC; }
+
+  for (int ax = 0; ax < 3; ++ax) {
+    int o1ax = ax == 0 ? 1 : 0;      // the two other axes, in index order
+    int o2ax = ax == 2 ? 1 : 2;
+    int nf = periodic[ax] ? m.n[ax] : m.n[ax] + 1;
+    for (int o1 = 0; o1 < m.n[o1ax]; ++o1)
+      for (int o2 = 0; o2 < m.n[o2ax]; ++o2)
+        for (int f = 0; f < nf; ++f) {
+          // the face between cell f-1 (lower) and cell f (upper) along ax
+          int base[3];
+          base[o1ax] = o1; base[o2ax] = o2; base[ax] = 0;
+          double S[3];
+          m.face_vector(ax, f, o1, o2, S);
+          double area = std::sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
+          if (area == 0.0) continue;  // pole faces carry no flux
+          double nvec[3] = {S[0] / area, S[1] / area, S[2] / area};
+
+          bool lower_in = periodic[ax] || f >= 1;
+          bool upper_in = periodic[ax] || f <= m.n[ax] - 1;
+          int lo = f - 1, up = f;
+          int cl[3], cu[3];
+          shift(ax, lo, base, cl);
+          shift(ax, up, base, cu);
+
+          T wl[9], wr[9];
+          const T* Wl = st.at(cl[0], cl[1], cl[2]);
+          const T* Wu = st.at(cu[0], cu[1], cu[2]);
+          if (!(lower_in && upper_in)) {
+            // physical boundary face: first-order ghost / interior states
+            for (int v = 0; v < 9; ++v) { wl[v] = Wl[v]; wr[v] = Wu[v]; }
+          } else {
+            int cll[3], cuu[3];
+            shift(ax, lo - 1, base, cll);
+            shift(ax, up + 1, base, cuu);
+            const T* Wll = st.at(cll[0], cll[1], cll[2]);
+            const T* Wuu = st.at(cuu[0], cuu[1], cuu[2]);
+            Spacing sl = spacing(m, ax, lo), su = spacing(m, ax, up);
+            for (int v = 0; v < 9; ++v) {
+              T slope_l = limited_slope((Wl[v] - Wll[v]) / sl.dm, (Wu[v] - Wl[v]) / sl.dp,
+                                        m.d.limiter, m.d.lim_eps);
+              T slope_u = limited_slope((Wu[v] - Wl[v]) / su.dm, (Wuu[v] - Wu[v]) / su.dp,
+                                        m.d.limiter, m.d.lim_eps);
+              wl[v] = Wl[v] + slope_l * sl.hp;
+              wr[v] = Wu[v] - slope_u * su.hm;
+            }
+          }
+          T F[9], lam;
+          rusanov_flux(wl, wr, nvec, gamma, ch, F, lam);
+          long il = -1, iu = -1;
+          if (lower_in) {
+            int a = periodic[ax] ? ((lo % m.n[ax]) + m.n[ax]) % m.n[ax] : lo;
+            cl[ax] = a;
+            il = m.idx(cl[0], cl[1], cl[2]);
+          }
+          if (upper_in) {
+            int a = periodic[ax] ? up % m.n[ax] : up;
+            cu[ax] = a;
+            iu = m.idx(cu[0], cu[1], cu[2]);
+          }
+          for (int v = 0; v < 9; ++v) {
+            T fs = F[v] * area;
+            if (il >= 0) { res.R[v * N + il] -= fs; res.scale[v * N + il] += std::fabs(val(fs)); }
+            if (iu >= 0) { res.R[v * N + iu] += fs; res.scale[v * N + iu] += std::fabs(val(fs)); }
+          }
+          if (il >= 0) res.lam[il] += val(lam) * area;
+          if (iu >= 0) res.lam[iu] += val(lam) * area;
+          if (m.d.geom == GEOM_SPHERE && ax == 0) {
+            if (f == 0) for (int v = 0; v < 9; ++v) res.bin[v] += F[v] * area;
+            if (f == m.n[0]) for (int v = 0; v < 9; ++v) res.bout[v] += F[v] * area;
+          }
+        }
+  }
+
+  // divide by the volume, add the gravity source [Sect. 2.2: rho g in the
+  // momentum equation, rho g.V in the energy equation; g = -g0 rhat / r^2]
+  for (int a = 0; a < m.n[0]; ++a)
+    for (int b = 0; b < m.n[1]; ++b)
+      for (int c = 0; c < m.n[2]; ++c) {
+        long id = m.idx(a, b, c);
+        double vol = m.volume(a, b, c);
+        for (int v = 0; v < 9; ++v) {
+          res.R[v * N + id] = res.R[v * N + id] / vol;
+          res.scale[v * N + id] /= vol;
+        }
+        if (m.d.geom == GEOM_SPHERE && m.d.g0 != 0.0) {
+          double e[3];
+          m.rhat(b, c, e);
+          double r = m.rc(a);
+          double g[3] = {-m.d.g0 * e[0] / (r * r), -m.d.g0 * e[1] / (r * r), -m.d.g0 * e[2] / (r * r)};
+          T rho = U[U_RHO * N + id];
+          T mg = U[U_MX * N + id] * g[0] + U[U_MY * N + id] * g[1] + U[U_MZ * N + id] * g[2];
+          res.R[U_MX * N + id] += rho * g[0];
+          res.R[U_MY * N + id] += rho * g[1];
+          res.R[U_MZ * N + id] += rho * g[2];
+          res.R[U_E * N + id] += mg;
+        }
+      }
+}
+
+bool desc_ok(const orc_desc* d) {
+  if (!d) return false;
+  if (d->n0 < 1 || d->n1 < 1 || d->n2 < 1) return false;
+  if (d->geom == GEOM_SPHERE) {
+    if (d->n2 % 2 != 0) return false;  // across-pole ghosts need an even N_phi
+    if (!(d->r_in > 0.0 && d->r_out > d->r_in)) return false;
+    if (d->n0 < 2) return false;
+  } else if (d->geom != GEOM_BOX) {
+    return false;
+  }
+  return d->gamma > 1.0;
+}
+
+}  // namespace
+
+extern "C" {
+
+// R = dU/dt for conservative SoA U[9][N]; Br[N_theta][N_phi] (sphere only).
+// norms9 (optional): L2 norm of each residual variable over the cells.
+// dtmin (optional): min over cells of V / sum_f lambda_f |S_f|.
+// scale (optional): 9 x N flux-magnitude scale (1/V) sum_f |F*_v||S_f|.
+// bflux (optional): 18 values, sum over inner / outer boundary faces of F*|S|.
+int orc_residual(const orc_desc* d, const double* U, const double* Br, double* R,
+                 double* norms9, double* dtmin, double* scale, double* bflux) {
+  if (!desc_ok(d) || !U || !R) return 1;
+  if (d->geom == GEOM_SPHERE && !Br) return 1;
+  Mesh m(*d);
+  Residual<double> res;
+  residual_core(m, U, Br, res);
+  const long N = m.ncell;
+  std::memcpy(R, res.R.data(), sizeof(double) * 9 * N);
+  if (norms9) {
+    for (int v = 0; v < 9; ++v) {
+      double s = 0.0;
+      for (long c = 0; c < N; ++c) s += R[v * N + c] * R[v * N + c];
+      norms9[v] = std::sqrt(s);
+    }
+  }
+  if (dtmin) {
+    double best = INFINITY;
+    for (int a = 0; a < m.n[0]; ++a)
+      for (int b = 0; b < m.n[1]; ++b)
+        for (int c = 0; c < m.n[2]; ++c) {
+          long id = m.idx(a, b, c);
+          best = std::min(best, m.volume(a, b, c) / res.lam[id]);
+        }
+    *dtmin = best;
+  }
+  if (scale) std::memcpy(scale, res.scale.data(), sizeof(double) * 9 * N);
+  if (bflux) for (int v = 0; v < 9; ++v) { bflux[v] = res.bin[v]; bflux[9 + v] = res.bout[v]; }
+  return 0;
+}
+
+// Jacobian-vector product by forward-mode dual numbers: dR = (dR/dU) dU +
+// (dR/dBr) dBr.  R receives the residual value.
+int orc_residual_jvp(const orc_desc* d, const double* U, const double* Br,
+                     const double* dU, const double* dBr, double* R, double* dR) {
+  if (!desc_ok(d) || !U || !dU || !R || !dR) return 1;
+  if (d->geom == GEOM_SPHERE && (!Br || !dBr)) return 1;
+  Mesh m(*d);
+  const long N = m.ncell;
+  std::vector<Dual> Ud(9 * N);
+  for (long q = 0; q < 9 * N; ++q) Ud[q] = Dual(U[q], dU[q]);
+  std::vector<Dual> Bd;
+  if (d->geom == GEOM_SPHERE) {
+    long nc = (long)d->n1 * d->n2;
+    Bd.resize(nc);
+    for (long q = 0; q < nc; ++q) Bd[q] = Dual(Br[q], dBr[q]);
+  }
+  Residual<Dual> res;
+  residual_core(m, Ud.data(), Bd.empty() ? nullptr : Bd.data(), res);
+  for (long q = 0; q < 9 * N; ++q) { R[q] = res.R[q].v; dR[q] = res.R[q].d; }
+  return 0;
+}
+
+// gravity-free flux helper for flux pins: Rusanov flux through unit normal n
+// for primitive left/right states; lam receives the dissipation speed.
+int orc_flux(const double* wl, const double* wr, const double* n, double gamma,
+             double ch, double* F, double* lam) {
+  if (!wl || !wr || !n || !F || !lam) return 1;
+  rusanov_flux(wl, wr, n, gamma, ch, F, *lam);
+  return 0;
+}
+
+// conversions for tests
+int orc_cons_to_prim(const orc_desc* d, const double* U, double* W) {
+  if (!desc_ok(d) || !U || !W) return 1;
+  long N = (long)d->n0 * d->n1 * d->n2;
+  for (long c = 0; c < N; ++c) {
+    double u[9], w[9];
+    for (int v = 0; v < 9; ++v) u[v] = U[v * N + c];
+    cons_to_prim(u, d->gamma, w);
+    for (int v = 0; v < 9; ++v) W[v * N + c] = w[v];
+  }
+  return 0;
+}
+
+// geometry for tests: vol[N]; S0[(n0+1) n1 n2 3], S1[n0 (n1+1) n2 3],
+// S2[n0 n1 (n2+1) 3] (face index along the axis, then the other two axes in
+// index order, then the Cartesian component).
+int orc_geometry(const orc_desc* d, double* vol, double* S0, double* S1, double* S2) {
+  if (!desc_ok(d)) return 1;
+  Mesh m(*d);
+  int n0 = m.n[0], n1 = m.n[1], n2 = m.n[2];
+  if (vol)
+    for (int a = 0; a < n0; ++a)
+      for (int b = 0; b < n1; ++b)
+        for (int c = 0; c < n2; ++c) vol[m.idx(a, b, c)] = m.volume(a, b, c);
+  if (S0)
+    for (int f = 0; f <= n0; ++f)
+      for (int b = 0; b < n1; ++b)
+        for (int c = 0; c < n2; ++c) m.face_vector(0, f, b, c, &S0[3 * (((long)f * n1 + b) * n2 + c)]);
+  if (S1)
+    for (int a = 0; a < n0; ++a)
+      for (int f = 0; f <= n1; ++f)
+        for (int c = 0; c < n2; ++c) m.face_vector(1, f, a, c, &S1[3 * (((long)a * (n1 + 1) + f) * n2 + c)]);
+  if (S2)
+    for (int a = 0; a < n0; ++a)
+      for (int b = 0; b < n1; ++b)
+        for (int f = 0; f <= n2; ++f) m.face_vector(2, f, a, b, &S2[3 * (((long)a * n1 + b) * (n2 + 1) + f)]);
+  return 0;
+}
+
+// ghost planes for tests (sphere): Win / Wout [9][n1][n2] primitive ghosts.
+int orc_ghosts(const orc_desc* d, const double* U, const double* Br, double* Win, double* Wout) {
+  if (!desc_ok(d) || d->geom != GEOM_SPHERE || !U || !Br) return 1;
+  Mesh m(*d);
+  State<double> st(m, U, Br);
+  long nc = (long)d->n1 * d->n2;
+  for (long c = 0; c < nc; ++c)
+    for (int v = 0; v < 9; ++v) {
+      if (Win) Win[v * nc + c] = st.Gin[9 * c + v];
+      if (Wout) Wout[v * nc + c] = st.Gout[9 * c + v];
+    }
+  return 0;
+}
+
+// Explicit pseudo-time stepping U <- U + dt R(U), dt = cfl * dtmin(U), with
+// the res(a) monitor of Sect. 2.1: res_log10[step][v] = log10 ||a^t - a^{t+1}||_2
+// over the nine primitive variables a.  U is updated in place.
+int orc_pseudo_time_step(const orc_desc* d, double* U, const double* Br, int nsteps,
+                         double cfl, double* res_log10, double* dt_out) {
+  if (!desc_ok(d) || !U || nsteps < 0) return 1;
+  Mesh m(*d);
+  const long N = m.ncell;
+  std::vector<double> R(9 * N), W0(9 * N), W1(9 * N);
+  for (int s = 0; s < nsteps; ++s) {
+    double dtmin;
+    int rc = orc_residual(d, U, Br, R.data(), nullptr, &dtmin, nullptr, nullptr);
+    if (rc) return rc;
+    double dt = cfl * dtmin;
+    orc_cons_to_prim(d, U, W0.data());
+    for (long q = 0; q < 9 * N; ++q) U[q] = U[q] + dt * R[q];
+    orc_cons_to_prim(d, U, W1.data());
+    if (res_log10)
+      for (int v = 0; v < 9; ++v) {
+        double acc = 0.0;
+        for (long c = 0; c < N; ++c) {
+          double diff = W0[v * N + c] - W1[v * N + c];
+          acc += diff * diff;
+        }
+        res_log10[s * 9 + v] = std::log10(std::sqrt(acc));
+      }
+    if (dt_out) dt_out[s] = dt;
+  }
+  return 0;
+}
+
+}  // extern "C"
