@@ -1,0 +1,156 @@
+/*
+ * corona.h -- C ABI of the GB300 (sm_103a) library for the finite-volume
+ * ideal-MHD + GLM residual of a global coronal model (arXiv 2209.04481).
+ *
+ * The operator: on a spherical shell r in [r_in, r_out] (1 -> 21.5 R_sun) with
+ * N_r x N_theta x N_phi cells (geometric radial stretch, uniform theta and phi,
+ * poles included), the residual R = dU/dt of the conservative state
+ * U = (rho, rho V, B, E, psi):
+ *   - ideal MHD in Alfven-speed units with gravity (Sect. 2.2 system; the
+ *     printed 8 pi / 4 pi factors are absorbed by the Sect. 2.1 reference
+ *     values), E = p/(gamma-1) + rho V^2/2 + B^2/2;
+ *   - second-order finite volumes (Sect. 2.1) with limited linear
+ *     reconstruction of the primitives (rho, V, B, p, psi);
+ *   - Rusanov face fluxes with GLM hyperbolic divergence cleaning, cleaning
+ *     speed c_h (Sect. 2.1; c_h = 1 in Sect. 3.3);
+ *   - inner boundary of Sect. 3.2 ("low E"): B_r prescribed from a
+ *     magnetogram, B_theta and B_phi Neumann, V_b parallel to B_b so that
+ *     E_b = -V_b x B_b = 0, psi_b = 0 (Sect. 3.3);
+ *   - outer boundary of Sect. 4.1 / Table 2 (rho, p ~ r^-a, B_r ~ r^-b,
+ *     psi_b = 0), across-pole theta ghosts, periodic phi;
+ *   - gravity source rho g, rho g.V (Sect. 2.2), g = -g0 rhat / r^2;
+ *   - the residual monitor res(a) = log10 ||a^t - a^{t+1}||_2 of Sect. 2.1.
+ *
+ * Layout of every state-like array: structure of arrays, variable-major,
+ * U[v][k][j][i] with v = 0..8 (rho, rho Vx, rho Vy, rho Vz, Bx, By, Bz, E, psi),
+ * k = r index, j = theta index, i = phi index (contiguous).  Vector components
+ * are Cartesian.  Element type: double for CRN_FP64 grids, float for
+ * CRN_FP32_BULK grids (the bulk flux arithmetic in FP32; pressure recovery in
+ * low-beta cells, norms and the pseudo-time update in FP64).
+ *
+ * Pointers named *_dev are device pointers on the grid's device; the library
+ * never frees caller memory and allocates only in crn_grid_create.  All
+ * compute calls are asynchronous on the given stream (a cudaStream_t passed as
+ * void*, NULL = the legacy default stream) and never synchronise, except
+ * crn_sync_status.  Functions return a crn_status; argument errors are
+ * reported synchronously, errors detected by kernels are sticky in the grid's
+ * device error word until crn_sync_status reads and clears them.
+ */
+#ifndef CORONA_H
+#define CORONA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CRN_OK = 0,
+  CRN_E_ARG = 1,          /* bad pointer, size, layout or descriptor field      */
+  CRN_E_CUDA = 2,         /* CUDA runtime / launch error (text: crn_last_error)  */
+  CRN_E_NONPHYSICAL = 3,  /* kernel saw rho <= 0, p <= 0 or a non-finite value   */
+  CRN_E_TIMEOUT = 4,      /* a bounded device wait gave up                       */
+  CRN_E_STATE = 5         /* call out of order (e.g. no inner boundary set)      */
+} crn_status;
+
+typedef enum { CRN_FP64 = 0, CRN_FP32_BULK = 1 } crn_precision;
+typedef enum { CRN_LIM_NONE = 0, CRN_LIM_MINMOD = 1, CRN_LIM_VANALBADA = 2 } crn_limiter;
+typedef enum { CRN_KERNEL_TILED = 0, CRN_KERNEL_CELLWISE = 1 } crn_kernel;
+
+/* Grid and physics description.  crn_grid_desc_default fills the solar-wind
+ * defaults: r in [1, 21.5], gamma = 1.05, c_h = 1, g0 = 0.8271 (G M_sun /
+ * (R_sun V_ref^2) with V_ref = B_ref / sqrt(mu0 rho_ref) of Sect. 2.1), van
+ * Albada limiter with eps = 1e-12, outer exponents a = b = 2 (Table 2 case 3),
+ * rho_b = 1, p_b = 0.0827, FP32_BULK, tiled kernel. */
+typedef struct {
+  int32_t n_r, n_theta, n_phi;  /* cells; n_phi even and a multiple of 8         */
+  int32_t precision;            /* crn_precision                                 */
+  int32_t limiter;              /* crn_limiter                                   */
+  int32_t kernel;               /* crn_kernel (CELLWISE: simple reference kernel) */
+  double r_in, r_out;           /* shell radii, 0 < r_in < r_out                 */
+  double gamma;                 /* ratio of specific heats, > 1                  */
+  double c_h;                   /* GLM cleaning speed, >= 0                      */
+  double g0;                    /* gravity: g = -g0 rhat / r^2                   */
+  double lim_eps;               /* van Albada epsilon, >= 0                      */
+  double outer_rho_exp;         /* outer ghost rho, p scaled by (r_I/r_G)^a      */
+  double outer_br_exp;          /* outer ghost B_r scaled by (r_I/r_G)^b         */
+  double rho_b, p_b;            /* inner boundary density and pressure, > 0      */
+} crn_grid_desc;
+
+typedef struct crn_grid crn_grid;
+
+/* Fill *d with the defaults above for an n_r x n_theta x n_phi shell.
+ * Returns CRN_E_ARG if d is NULL. */
+int crn_grid_desc_default(crn_grid_desc* d, int32_t n_r, int32_t n_theta, int32_t n_phi);
+
+/* Create a grid on the current CUDA device: validates *d (CRN_E_ARG with a
+ * message on any bad field), computes the exact face-area vectors and volumes
+ * of the shell on the host in FP64 as 1D radial factors times per-column
+ * angular factors and unit normals, uploads them (cast once to FP32 for
+ * FP32_BULK grids), and allocates the grid-owned scratch: reduction partials,
+ * error word, B_r copy, and the residual / FP32 shadow buffers used by
+ * crn_pseudo_time_step.  *out receives the handle (NULL on error).
+ * Synchronous.  Thread-compatible: one grid must not be used from two host
+ * threads at once. */
+int crn_grid_create(const crn_grid_desc* d, crn_grid** out);
+
+/* Free everything crn_grid_create allocated (synchronises the device first).
+ * NULL is accepted. */
+int crn_grid_destroy(crn_grid* g);
+
+/* Prescribe the inner-boundary radial field B_r [Sect. 1 and 3.2: B_r from the
+ * magnetogram at the inner boundary].  Br_dev: FP64 device array
+ * [n_theta][n_phi], B_r at the inner face centres (theta_c, phi_c); copied
+ * into grid-owned storage asynchronously on the stream (the caller may reuse
+ * its buffer once the stream has passed this point).  Must precede the first
+ * residual / pseudo-time call (CRN_E_STATE otherwise). */
+int crn_set_inner_boundary(crn_grid* g, const double* Br_dev, void* stream);
+
+/* One residual evaluation R = dU/dt (per unit volume).  U_dev, R_dev: caller
+ * device buffers of 9 * n_r * n_theta * n_phi elements of the grid's precision
+ * (double for FP64, float for FP32_BULK), SoA layout above; they must not
+ * overlap.  norms9_dev (optional, may be NULL): 9 doubles, the L2 norm over the
+ * cells of each residual variable.  dtmin_dev (optional): 1 double,
+ * min over cells of V_c / sum_f lambda_f |S_f| (the explicit step bound at
+ * CFL 1).  Asynchronous; no allocation; no host synchronisation. */
+int crn_residual(crn_grid* g, const void* U_dev, void* R_dev, double* norms9_dev,
+                 double* dtmin_dev, void* stream);
+
+/* Vector-Jacobian product of the residual: Ubar = (dR/dU)^T Rbar (same layout
+ * and precision as U) and Brbar = (dR/dB_r)^T Rbar (FP64 [n_theta][n_phi]),
+ * both overwritten.  Rbar_dev has the layout of R.  Brbar_dev may be NULL. */
+int crn_residual_vjp(crn_grid* g, const void* U_dev, const void* Rbar_dev, void* Ubar_dev,
+                     double* Brbar_dev, void* stream);
+
+/* nsteps explicit pseudo-time steps U <- U + dt R(U), dt = cfl * dtmin(U),
+ * on the FP64 master state U64_dev (9 * N doubles, updated in place) [the
+ * paper's solver steps in pseudo-time to a steady state, Sect. 2.1].  FP32_BULK
+ * grids evaluate R on an FP32 shadow of the master and update the master in
+ * FP64.  res_log10_dev (optional): nsteps x 9 doubles, the res(a) monitor of
+ * Sect. 2.1 for the nine primitives a = (rho, Vx, Vy, Vz, Bx, By, Bz, p, psi):
+ * log10 of the L2 norm over the cells of a^t - a^{t+1}.  No host
+ * synchronisation; the sequence of launches can be captured in a CUDA graph. */
+int crn_pseudo_time_step(crn_grid* g, double* U64_dev, int32_t nsteps, double cfl,
+                         double* res_log10_dev, void* stream);
+
+/* Synchronise the stream, then read and clear the grid's device error word.
+ * Returns CRN_E_NONPHYSICAL if a kernel saw a non-physical state since the
+ * last call (crn_last_bad_cell gives the lowest flagged cell index,
+ * k * n_theta * n_phi + j * n_phi + i), CRN_E_CUDA on a CUDA error. */
+int crn_sync_status(crn_grid* g, void* stream);
+
+/* Lowest flat cell index flagged by the last crn_sync_status, -1 if none. */
+int64_t crn_last_bad_cell(const crn_grid* g);
+
+/* Message of the last error returned on the calling host thread ("" if none). */
+const char* crn_last_error(void);
+
+/* Number of kernel launches the last compute call of this grid issued. */
+int32_t crn_last_launch_count(const crn_grid* g);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CORONA_H */

@@ -1,0 +1,240 @@
+"""GB300 (sm_103a) library for the MHD + GLM residual of a global coronal model.
+
+Thin Python binding of the C ABI in ``include/corona.h`` (argument marshalling
+only: every step of the residual runs in the library's CUDA kernels).  PyTorch
+provides device memory and streams.  The library is built in-tree by
+``paper_2209_04481_gb300.build`` (nvcc, sm_103a); if it cannot be built or
+loaded, importing the binding raises -- there is no CPU fallback.
+
+Paper: arXiv 2209.04481 (Brchnelova et al., "To E or not to E: Numerical
+Nuances of Global Coronal Models"): second-order finite volumes with
+hyperbolic divergence cleaning (Sect. 2.1), ideal MHD with gravity
+(Sect. 2.2), the low-E inner boundary (Sect. 3.2) and the outer extrapolation
+laws (Sect. 4.1, Table 2).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+__all__ = ["Grid", "load_library", "CoronaError", "FP64", "FP32_BULK", "LIMITERS",
+           "KERNEL_TILED", "KERNEL_CELLWISE", "exported_symbols"]
+
+FP64, FP32_BULK = 0, 1
+KERNEL_TILED, KERNEL_CELLWISE = 0, 1
+LIMITERS = {"none": 0, "minmod": 1, "vanalbada": 2}
+_STATUS = {0: "CRN_OK", 1: "CRN_E_ARG", 2: "CRN_E_CUDA", 3: "CRN_E_NONPHYSICAL",
+           4: "CRN_E_TIMEOUT", 5: "CRN_E_STATE"}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_lock = threading.Lock()
+_lib = None
+
+
+class CoronaError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [
+        ("n_r", ctypes.c_int32), ("n_theta", ctypes.c_int32), ("n_phi", ctypes.c_int32),
+        ("precision", ctypes.c_int32), ("limiter", ctypes.c_int32), ("kernel", ctypes.c_int32),
+        ("r_in", ctypes.c_double), ("r_out", ctypes.c_double),
+        ("gamma", ctypes.c_double), ("c_h", ctypes.c_double), ("g0", ctypes.c_double),
+        ("lim_eps", ctypes.c_double),
+        ("outer_rho_exp", ctypes.c_double), ("outer_br_exp", ctypes.c_double),
+        ("rho_b", ctypes.c_double), ("p_b", ctypes.c_double),
+    ]
+
+
+def library_path() -> str:
+    from . import build as _build
+    return _build.LIB
+
+
+def load_library(build_if_needed: bool = True):
+    """Load libcorona.so (building it with nvcc first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        from . import build as _build
+        if build_if_needed:
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError("libcorona.so is missing and could not be built")
+        lib = ctypes.CDLL(_build.LIB)
+        vp, i32, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_double
+        D = ctypes.POINTER(GridDesc)
+        sigs = {
+            "crn_grid_desc_default": (ctypes.c_int, [D, i32, i32, i32]),
+            "crn_grid_create": (ctypes.c_int, [D, ctypes.POINTER(vp)]),
+            "crn_grid_destroy": (ctypes.c_int, [vp]),
+            "crn_set_inner_boundary": (ctypes.c_int, [vp, vp, vp]),
+            "crn_residual": (ctypes.c_int, [vp, vp, vp, vp, vp, vp]),
+            "crn_residual_vjp": (ctypes.c_int, [vp, vp, vp, vp, vp, vp]),
+            "crn_pseudo_time_step": (ctypes.c_int, [vp, vp, i32, dbl, vp, vp]),
+            "crn_sync_status": (ctypes.c_int, [vp, vp]),
+            "crn_last_bad_cell": (ctypes.c_int64, [vp]),
+            "crn_last_error": (ctypes.c_char_p, []),
+            "crn_last_launch_count": (i32, [vp]),
+        }
+        for name, (res, args) in sigs.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def exported_symbols():
+    """Names of the C ABI functions the header declares (parsed from include/corona.h)."""
+    import re
+    hdr = os.path.join(os.path.dirname(_HERE), "include", "corona.h")
+    with open(hdr) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"^\s*[\w\s\*]*?\b(crn_\w+)\s*\(", text, flags=re.M)))
+
+
+def _check(rc):
+    if rc != 0:
+        msg = _lib.crn_last_error().decode(errors="replace")
+        raise CoronaError(rc, msg)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Grid:
+    """A spherical-shell grid on the current CUDA device (``crn_grid``).
+
+    Parameters mirror ``crn_grid_desc``; unspecified ones take the library
+    defaults of ``crn_grid_desc_default`` (r in [1, 21.5], gamma = 1.05,
+    c_h = 1, solar g0, van Albada, Table 2 case 3 outer law).
+    """
+
+    def __init__(self, n_r, n_theta, n_phi, precision="fp32", limiter="vanalbada",
+                 kernel="tiled", **kw):
+        lib = load_library()
+        d = GridDesc()
+        _check(lib.crn_grid_desc_default(ctypes.byref(d), n_r, n_theta, n_phi))
+        d.precision = {"fp64": FP64, "fp32": FP32_BULK, "fp32_bulk": FP32_BULK}[precision]
+        d.limiter = LIMITERS[limiter]
+        d.kernel = {"tiled": KERNEL_TILED, "cellwise": KERNEL_CELLWISE}[kernel]
+        for k, v in kw.items():
+            if not hasattr(d, k):
+                raise TypeError(f"unknown grid parameter {k}")
+            setattr(d, k, v)
+        self.desc = d
+        h = ctypes.c_void_p()
+        _check(lib.crn_grid_create(ctypes.byref(d), ctypes.byref(h)))
+        self._h = h
+        self.shape = (n_r, n_theta, n_phi)
+        self.ncell = n_r * n_theta * n_phi
+        self.precision = precision
+        self._br = None
+
+    # -- lifetime ----------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.crn_grid_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def dtype(self):
+        import torch
+        return torch.float64 if self.desc.precision == FP64 else torch.float32
+
+    @property
+    def last_launch_count(self):
+        return int(_lib.crn_last_launch_count(self._h))
+
+    # -- calls ---------------------------------------------------------------
+    def set_inner_boundary(self, Br, stream=None):
+        """Prescribe B_r[n_theta, n_phi] (FP64 CUDA tensor) at the inner face centres."""
+        import torch
+        if Br.dtype != torch.float64 or not Br.is_cuda or not Br.is_contiguous():
+            raise ValueError("Br must be a contiguous float64 CUDA tensor")
+        if tuple(Br.shape) != self.shape[1:]:
+            raise ValueError(f"Br must have shape {self.shape[1:]}")
+        _check(_lib.crn_set_inner_boundary(self._h, _ptr(Br), _stream_handle(stream)))
+        self._br = Br
+
+    def _state_check(self, t, name, dtype=None):
+        dtype = dtype or self.dtype
+        if t.dtype != dtype or not t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous {dtype} CUDA tensor")
+        if t.numel() != 9 * self.ncell:
+            raise ValueError(f"{name} must hold 9 x {self.shape} elements")
+
+    def residual(self, U, R=None, norms=None, dtmin=None, stream=None):
+        """R = dU/dt for U of shape (9, n_r, n_theta, n_phi) in the grid's dtype."""
+        import torch
+        self._state_check(U, "U")
+        if R is None:
+            R = torch.empty_like(U)
+        self._state_check(R, "R")
+        _check(_lib.crn_residual(self._h, _ptr(U), _ptr(R), _ptr(norms), _ptr(dtmin),
+                                 _stream_handle(stream)))
+        return R
+
+    def residual_vjp(self, U, Rbar, Ubar=None, Brbar=None, stream=None):
+        import torch
+        self._state_check(U, "U")
+        self._state_check(Rbar, "Rbar")
+        if Ubar is None:
+            Ubar = torch.empty_like(U)
+        _check(_lib.crn_residual_vjp(self._h, _ptr(U), _ptr(Rbar), _ptr(Ubar), _ptr(Brbar),
+                                     _stream_handle(stream)))
+        return Ubar, Brbar
+
+    def pseudo_time_step(self, U64, nsteps, cfl, res_log10=None, stream=None):
+        """nsteps explicit steps on the FP64 master state U64 (in place)."""
+        import torch
+        self._state_check(U64, "U64", torch.float64)
+        _check(_lib.crn_pseudo_time_step(self._h, _ptr(U64), int(nsteps), float(cfl),
+                                         _ptr(res_log10), _stream_handle(stream)))
+        return U64
+
+    def sync_status(self, stream=None):
+        """Synchronise and raise CoronaError if a kernel flagged a non-physical state."""
+        _check(_lib.crn_sync_status(self._h, _stream_handle(stream)))
+
+    @property
+    def last_bad_cell(self):
+        return int(_lib.crn_last_bad_cell(self._h))
+
+    def residual_host(self, U_host, R_host, norms=None, dtmin=None, stream=None):
+        """End-to-end call on host (pinned) buffers: copy U in, evaluate, copy R out.
+
+        Uses device staging tensors allocated once per grid; the copies and the
+        kernel run in order on ``stream``.
+        """
+        import torch
+        if not hasattr(self, "_stage"):
+            self._stage = (torch.empty((9,) + self.shape, dtype=self.dtype, device="cuda"),
+                           torch.empty((9,) + self.shape, dtype=self.dtype, device="cuda"))
+        Ud, Rd = self._stage
+        s = stream or torch.cuda.current_stream()
+        with torch.cuda.stream(s):
+            Ud.copy_(U_host, non_blocking=True)
+            self.residual(Ud, Rd, norms, dtmin, stream=s)
+            R_host.copy_(Rd, non_blocking=True)
+        return R_host

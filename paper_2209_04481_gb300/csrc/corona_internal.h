@@ -1,0 +1,68 @@
+// corona_internal.h -- host-side grid object and kernel launchers shared by
+// the translation units of libcorona (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/corona.h"
+#include "mhd_device.cuh"
+
+namespace crn {
+
+struct Reduce;
+
+// device geometry of one precision (one allocation, carved into arrays)
+template <class T>
+struct GeoBuf {
+  T* base = nullptr;
+  Geo<T> geo{};
+};
+
+struct LaunchCfg {
+  int kchunk_tiled = 16;  // radial planes per CTA of the tiled kernel
+};
+
+}  // namespace crn
+
+struct crn_grid {
+  crn_grid_desc d;
+  int device = 0;
+  crn::Shape shape{};
+  crn::Phys<double> ph64{};
+  crn::Phys<float> ph32{};
+  crn::GeoBuf<double> g64;
+  crn::GeoBuf<float> g32;
+  double* br = nullptr;            // [nt][np] prescribed B_r
+  bool have_br = false;
+  double* partials = nullptr;      // reduction partials [max_blocks][16]
+  size_t max_blocks = 0;
+  unsigned int* counter = nullptr; // CTA arrival counter
+  double* stats = nullptr;         // [0..8] norms, [9] dtmin
+  unsigned int* err_flags = nullptr;
+  unsigned long long* err_cell = nullptr;
+  void* rbuf = nullptr;            // residual scratch for pseudo-time stepping (9N of T)
+  float* shadow = nullptr;         // FP32 shadow of the master state (FP32_BULK)
+  int64_t last_bad_cell = -1;
+  int32_t last_launches = 0;
+  crn::LaunchCfg cfg;
+};
+
+namespace crn {
+
+// launchers (return cudaGetLastError() of the launch)
+cudaError_t launch_residual_fp64(crn_grid* g, const double* U, double* R, double* norms_user,
+                                 double* dt_user, cudaStream_t st, int* nlaunch);
+cudaError_t launch_residual_fp32(crn_grid* g, const float* U, float* R, double* norms_user,
+                                 double* dt_user, cudaStream_t st, int* nlaunch);
+cudaError_t launch_update(crn_grid* g, double* U64, double cfl, double* res_out,
+                          cudaStream_t st, int* nlaunch);
+cudaError_t launch_shadow(crn_grid* g, const double* U64, cudaStream_t st, int* nlaunch);
+
+// shared-memory footprint of the tiled kernel for one precision
+size_t tiled_smem_fp64();
+size_t tiled_smem_fp32();
+cudaError_t prepare_fp64();
+cudaError_t prepare_fp32();
+
+}  // namespace crn

@@ -1,0 +1,13 @@
+// residual_fp32.cu -- FP32-bulk instantiation of the residual kernels (FP32
+// flux arithmetic; FP64 pressure recovery in low-beta cells, FP64 ghost
+// vector algebra at the inner boundary, FP64 cross-thread reductions).
+#include "residual_launch.cuh"
+
+namespace crn {
+cudaError_t launch_residual_fp32(crn_grid* g, const float* U, float* R, double* norms_user,
+                                 double* dt_user, cudaStream_t st, int* nlaunch) {
+  return launch_residual_t<float>(g, U, R, norms_user, dt_user, st, nlaunch);
+}
+size_t tiled_smem_fp32() { return tiled_smem_t<float>(); }
+cudaError_t prepare_fp32() { return prepare_t<float>(); }
+}  // namespace crn

@@ -1,0 +1,88 @@
+// residual_launch.cuh -- host launcher of the residual kernels for one
+// precision; included by residual_fp64.cu and residual_fp32.cu so that the
+// two instantiations compile as separate translation units.
+#pragma once
+
+#include "corona_internal.h"
+#include "residual.cuh"
+
+namespace crn {
+
+template <class T> struct TileFor;
+template <> struct TileFor<double> { static constexpr int TT = 4, TP = 32; };
+template <> struct TileFor<float> { static constexpr int TT = 8, TP = 32; };
+
+template <class T> const Geo<T>& geo_of(const crn_grid* g);
+template <> inline const Geo<double>& geo_of<double>(const crn_grid* g) { return g->g64.geo; }
+template <> inline const Geo<float>& geo_of<float>(const crn_grid* g) { return g->g32.geo; }
+template <class T> const Phys<T>& phys_of(const crn_grid* g);
+template <> inline const Phys<double>& phys_of<double>(const crn_grid* g) { return g->ph64; }
+template <> inline const Phys<float>& phys_of<float>(const crn_grid* g) { return g->ph32; }
+
+inline Reduce make_reduce(crn_grid* g, double* norms_user, double* dt_user) {
+  Reduce r;
+  r.partials = g->partials;
+  r.counter = g->counter;
+  r.norms_out = g->stats;
+  r.dt_out = g->stats + 9;
+  r.norms_user = norms_user;
+  r.dt_user = dt_user;
+  r.err_flags = g->err_flags;
+  r.err_cell = g->err_cell;
+  r.log_out = nullptr;
+  return r;
+}
+
+template <class T, int LIM>
+cudaError_t launch_lim(crn_grid* g, const T* U, T* R, double* nu, double* du, cudaStream_t st) {
+  const Shape sh = g->shape;
+  const Geo<T>& geo = geo_of<T>(g);
+  const Phys<T>& ph = phys_of<T>(g);
+  const Reduce red = make_reduce(g, nu, du);
+  if (g->d.kernel == CRN_KERNEL_CELLWISE) {
+    const unsigned nb = (unsigned)((sh.ncell + 255) / 256);
+    residual_cellwise<T, LIM><<<nb, 256, 0, st>>>(sh, geo, ph, g->br, U, R, red);
+    return cudaGetLastError();
+  }
+  constexpr int TT = TileFor<T>::TT, TP = TileFor<T>::TP;
+  using D = TileDims<TT, TP>;
+  const size_t smem = D::template smem_bytes<T>();
+  const int ntiles = ((sh.nt + TT - 1) / TT) * ((sh.np + TP - 1) / TP);
+  const int kc = g->cfg.kchunk_tiled;
+  const int nch = (sh.nr + kc - 1) / kc;
+  dim3 grid((unsigned)ntiles, (unsigned)nch);
+  residual_tiled<T, LIM, TT, TP><<<grid, D::NT, smem, st>>>(sh, geo, ph, g->br, U, R, red, kc);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_residual_t(crn_grid* g, const T* U, T* R, double* nu, double* du,
+                              cudaStream_t st, int* nlaunch) {
+  *nlaunch = 1;
+  switch (g->d.limiter) {
+    case CRN_LIM_NONE: return launch_lim<T, 0>(g, U, R, nu, du, st);
+    case CRN_LIM_MINMOD: return launch_lim<T, 1>(g, U, R, nu, du, st);
+    default: return launch_lim<T, 2>(g, U, R, nu, du, st);
+  }
+}
+
+// opt the tiled kernels in to their dynamic shared memory on the current device
+template <class T>
+cudaError_t prepare_t() {
+  constexpr int TT = TileFor<T>::TT, TP = TileFor<T>::TP;
+  const int smem = (int)TileDims<TT, TP>::template smem_bytes<T>();
+  cudaError_t e;
+  e = cudaFuncSetAttribute(residual_tiled<T, 0, TT, TP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(residual_tiled<T, 1, TT, TP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(residual_tiled<T, 2, TT, TP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+template <class T>
+size_t tiled_smem_t() {
+  using D = TileDims<TileFor<T>::TT, TileFor<T>::TP>;
+  return D::template smem_bytes<T>();
+}
+
+}  // namespace crn

@@ -1,0 +1,55 @@
+"""The C-ABI library builds for sm_103a, loads, exports every declared entry
+point and validates descriptors on the host (no GPU needed)."""
+import ctypes
+
+import pytest
+
+import paper_2209_04481_gb300 as pg
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return pg.load_library()
+
+
+def test_header_declares_the_boundary():
+    names = pg.exported_symbols()
+    for required in ("crn_grid_create", "crn_grid_destroy", "crn_set_inner_boundary",
+                     "crn_residual", "crn_residual_vjp", "crn_pseudo_time_step",
+                     "crn_sync_status", "crn_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in pg.exported_symbols():
+        assert hasattr(lib, name), name
+
+
+def test_descriptor_defaults(lib):
+    d = pg.GridDesc()
+    assert lib.crn_grid_desc_default(ctypes.byref(d), 128, 64, 128) == 0
+    assert (d.n_r, d.n_theta, d.n_phi) == (128, 64, 128)
+    assert d.r_in == 1.0 and d.r_out == 21.5 and d.gamma == 1.05 and d.c_h == 1.0
+    assert abs(d.g0 - 0.82712) < 1e-4
+    assert d.precision == pg.FP32_BULK and d.limiter == pg.LIMITERS["vanalbada"]
+    assert d.outer_rho_exp == 2.0 and d.outer_br_exp == 2.0
+
+
+@pytest.mark.parametrize("field,value,needle", [
+    ("n_phi", 12, "n_phi"), ("n_r", 1, "n_r"), ("gamma", 1.0, "gamma"),
+    ("r_out", 0.5, "r_in"), ("precision", 7, "precision"), ("limiter", 9, "limiter"),
+    ("p_b", -1.0, "p_b"), ("c_h", -1.0, "c_h")])
+def test_create_rejects_bad_descriptors_before_any_device_work(lib, field, value, needle):
+    d = pg.GridDesc()
+    lib.crn_grid_desc_default(ctypes.byref(d), 8, 8, 16)
+    setattr(d, field, value)
+    h = ctypes.c_void_p()
+    assert lib.crn_grid_create(ctypes.byref(d), ctypes.byref(h)) == 1  # CRN_E_ARG
+    assert h.value is None
+    assert needle in lib.crn_last_error().decode()
+
+
+def test_null_arguments_are_rejected(lib):
+    assert lib.crn_residual(None, None, None, None, None, None) == 1
+    assert lib.crn_pseudo_time_step(None, None, 1, 0.4, None, None) == 1
+    assert lib.crn_grid_destroy(None) == 0
