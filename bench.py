@@ -1,0 +1,472 @@
+"""Benchmark: MHD + GLM residual throughput on the 128 x 64 x 128 coronal shell.
+
+One step = one residual evaluation R(U; B_r) of the whole shell through the
+C ABI (ghosts, primitive recovery, limited reconstruction, Rusanov + GLM face
+fluxes, accumulation + gravity, residual norms and the explicit step bound;
+the exact geometry is built once at grid creation).  Headline: the FP32-bulk
+path; the plain FP64 path and the explicit pseudo-time update are measured
+too and reported in sub-objects.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank evaluates its own independent shell
+(replicas; no collective on the data path) and rank 0 prints one JSON line
+with the whole-job throughput over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MHD residual cell-updates/s and HBM GB/s, FP32-bulk vs FP64 at stated error"
+WORKLOAD = "coronal shell 128x64x128 (r in [1,21.5] geometric, full sphere), Parker wind + dipole, " \
+           "inner B_r = dipole + l<=15 random field (seed 2209), max|B_r| = 5"
+SHAPE = (128, 64, 128)
+BYTES_PER_CELL = {"fp32": 72, "fp64": 144}     # read 9 + write 9 values per cell
+N_ROTATE = 4                                    # input/output sets rotated between steps
+KERNEL_SOURCES = ["paper_2209_04481_gb300/csrc/residual.cuh",
+                  "paper_2209_04481_gb300/csrc/mhd_device.cuh",
+                  "paper_2209_04481_gb300/csrc/residual_launch.cuh",
+                  "paper_2209_04481_gb300/csrc/residual_fp32.cu"]
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "residual_tiled_fp32_shell128.md")
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas only)
+# ---------------------------------------------------------------------------
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def init_dist(world, backend):
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend)
+    return dist if world > 1 else None
+
+
+def barrier(dist, device=None):
+    if dist is not None:
+        if device is not None:
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+def max_over_ranks(dist, value, device=None):
+    """Maximum of a float over ranks (the slowest rank's time)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device or "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate(units_per_rank, seconds_per_rank):
+    """Whole-job throughput: all ranks' units over the slowest rank's seconds."""
+    return sum(units_per_rank) / max(seconds_per_rank)
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self._t.join(timeout=2)
+
+    def summary(self):
+        mhz, maxes, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                mhz.append(float(parts[1]))
+                maxes.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, flag in zip(names, parts[5:9]):
+                if flag.lower() == "active":
+                    reasons.add(name)
+        if not mhz:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(mhz), "sm_max_mhz": max(maxes),
+                "reasons": sorted(reasons), "samples": len(mhz)}
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+def kernel_source_digest():
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel sources (else None)."""
+    try:
+        with open(PROFILE_SUMMARY) as f:
+            text = f.read()
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_digest") != kernel_source_digest():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def time_graph(torch, stream, fn_list, steps, warmup):
+    """Warm up, capture `steps` calls (cycling fn_list) into one CUDA graph and
+    time one replay with CUDA events on `stream`.  Returns seconds."""
+    with torch.cuda.stream(stream):
+        for i in range(warmup):
+            fn_list[i % len(fn_list)]()
+    stream.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        for i in range(steps):
+            fn_list[i % len(fn_list)]()
+    with torch.cuda.stream(stream):
+        g.replay()                               # one untimed replay (graph upload)
+    stream.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    return g, e0, e1
+
+
+# ---------------------------------------------------------------------------
+# the GB300 arm
+# ---------------------------------------------------------------------------
+def run_gb300(args):
+    import numpy as np
+    import torch
+
+    import coronal_inputs as ci
+    import paper_2209_04481_gb300 as pg
+
+    rank, world, local = dist_env()
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    dist = init_dist(world, "nccl")
+    pg.load_library()
+
+    # independent replica per rank: its own magnetogram seed
+    U0, info = ci.background(*SHAPE)
+    Br = ci.magnetogram(SHAPE[1], SHAPE[2], seed=2209 + rank)
+    ncell = int(np.prod(SHAPE))
+    stream = torch.cuda.Stream(device)
+    out = {}
+
+    def make(precision):
+        g = pg.Grid(*SHAPE, precision=precision, p_b=info["p_b"])
+        g.set_inner_boundary(torch.from_numpy(Br).to(device))
+        dt = torch.float32 if precision == "fp32" else torch.float64
+        Us = [torch.from_numpy(U0).to(device, dt) for _ in range(N_ROTATE)]
+        Rs = [torch.empty_like(Us[0]) for _ in range(N_ROTATE)]
+        norms = torch.zeros(9, dtype=torch.float64, device=device)
+        dtmin = torch.zeros(1, dtype=torch.float64, device=device)
+        calls = [(lambda q=q: g.residual(Us[q], Rs[q], norms, dtmin, stream=stream))
+                 for q in range(N_ROTATE)]
+        return g, Us, Rs, norms, dtmin, calls
+
+    # ---- headline: FP32-bulk residual
+    g32, Us, Rs, norms, dtmin, calls = make("fp32")
+    steps, warmup = args.steps, max(3, args.warmup)
+    graph, e0, e1 = time_graph(torch, stream, calls, steps, warmup)
+    barrier(dist, device)
+    torch.cuda.synchronize(device)
+    with ClockSampler(local) as clocks:
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            graph.replay()
+            e1.record(stream)
+        torch.cuda.synchronize(device)
+    barrier(dist, device)
+    sec = e0.elapsed_time(e1) / 1e3
+    sec_max = max_over_ranks(dist, sec, device)
+    g32.sync_status(stream)
+    value = aggregate([ncell * steps] * world, [sec_max])
+    kern_sec = sec / steps                     # one kernel launch per step
+    peak, peak_kind = measured_peaks()
+    achieved = BYTES_PER_CELL["fp32"] * ncell / kern_sec / 1e9
+    traffic = profiled_traffic()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": "residual_tiled<float,vanalbada,8,32>",
+                "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+    R32 = Rs[(steps - 1) % N_ROTATE].double().cpu().numpy()
+    del graph
+
+    # ---- e2e: host (pinned) buffers, copies inside the timed region
+    e2e_steps = max(3, min(steps, 200))
+    U_host = torch.from_numpy(U0.astype(np.float32)).pin_memory()
+    R_host = torch.empty_like(U_host).pin_memory()
+    norms_e2e = torch.zeros(9, dtype=torch.float64, device=device)
+    norms_host = torch.zeros(9, dtype=torch.float64).pin_memory()
+    for _ in range(3):
+        g32.residual_host(U_host, R_host, norms_e2e, stream=stream)
+    stream.synchronize()
+    barrier(dist, device)
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(e2e_steps):
+        g32.residual_host(U_host, R_host, norms_e2e, stream=stream)
+        with torch.cuda.stream(stream):
+            norms_host.copy_(norms_e2e, non_blocking=True)
+    a1.record(stream)
+    torch.cuda.synchronize(device)
+    e2e_sec = max_over_ranks(dist, a0.elapsed_time(a1) / 1e3, device)
+    e2e = {"value": aggregate([ncell * e2e_steps] * world, [e2e_sec]), "unit": "cell-updates/s",
+           "h2d_bytes_per_step": U_host.numel() * 4,
+           "d2h_bytes_per_step": R_host.numel() * 4 + norms_host.numel() * 8,
+           "steps": e2e_steps, "gpu_launches": e2e_steps,
+           "api": "Grid.residual_host -> crn_residual (pinned host buffers)"}
+
+    # ---- explicit pseudo-time update (FP32 bulk residual + FP64 master update),
+    # in batches of 10 steps from the initial state (forward Euler at CFL 0.4
+    # is only run for short stretches, as in the 10-step shell32 case)
+    U0d = torch.from_numpy(U0.copy()).to(device)
+    U64 = U0d.clone()
+    batch, nbatch = 10, max(1, min(steps // 40, 20))
+    with torch.cuda.stream(stream):
+        g32.pseudo_time_step(U64, 3, 0.4, stream=stream)
+    stream.synchronize()
+    pts_sec = 0.0
+    for _ in range(nbatch):
+        with torch.cuda.stream(stream):
+            U64.copy_(U0d)
+            p0 = torch.cuda.Event(enable_timing=True)
+            p1 = torch.cuda.Event(enable_timing=True)
+            p0.record(stream)
+            g32.pseudo_time_step(U64, batch, 0.4, stream=stream)
+            p1.record(stream)
+        torch.cuda.synchronize(device)
+        pts_sec += p0.elapsed_time(p1) / 1e3
+    g32.sync_status(stream)
+    pts_steps = batch * nbatch
+    pts = {"value": ncell * pts_steps / pts_sec, "unit": "cell-updates/s",
+           "ms_per_step": pts_sec * 1e3 / pts_steps, "steps": pts_steps, "cfl": 0.4,
+           "launches_per_step": 2,
+           "note": "residual on the FP32 shadow + FP64 master update and res(a) monitor; "
+                   f"{nbatch} batches of {batch} steps from the initial state"}
+    g32.close()
+    del Us, Rs, U64, U0d
+
+    # ---- plain FP64 residual
+    g64, Us, Rs, n64, d64, calls = make("fp64")
+    steps64 = max(3, min(steps // 40, 200))
+    graph, f0, f1 = time_graph(torch, stream, calls, steps64, 3)
+    with torch.cuda.stream(stream):
+        f0.record(stream)
+        graph.replay()
+        f1.record(stream)
+    torch.cuda.synchronize(device)
+    sec64 = max_over_ranks(dist, f0.elapsed_time(f1) / 1e3, device)
+    g64.sync_status(stream)
+    R64 = Rs[(steps64 - 1) % N_ROTATE].cpu().numpy()
+    fp64 = {"value": aggregate([ncell * steps64] * world, [sec64]), "unit": "cell-updates/s",
+            "ms_per_step": sec64 * 1e3 / steps64, "steps": steps64, "gpu_launches": steps64,
+            "hbm_gbs": BYTES_PER_CELL["fp64"] * ncell / (sec64 / steps64) / 1e9}
+    del graph
+    g64.close()
+
+    result = {
+        "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
+        "steps": steps, "warmup": warmup, "ms_per_step": sec_max * 1e3 / steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cells": ncell, "precision": "fp32-bulk (FP64 "
+                   "pressure recovery in low-beta cells, FP64 norms)", "limiter": "vanalbada",
+                   "l2": f"{N_ROTATE} rotating input/output sets "
+                         f"({N_ROTATE * 72 * ncell / 1e6:.0f} MB > L2)",
+                   "timing": "one CUDA graph of all timed steps, CUDA events on the launch stream",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roofline,
+        "hbm_gbs": achieved,
+        "e2e": e2e,
+        "gpu_launches": steps,
+        "clocks": clocks.summary(),
+        "fp64": fp64,
+        "pseudo_time_step": pts,
+    }
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"], err = cpu_baseline(U0, Br, info, R32, R64)
+        result["error_vs_oracle"] = err
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(U0, Br, info, R32=None, R64=None, budget_s=15.0):
+    """Time the FP64 CPU oracle on full shell evaluations (single thread) and use
+    its output to state the GPU results' error."""
+    import numpy as np
+
+    import coronal_inputs as ci
+    import oracle
+
+    og = oracle.Grid(*SHAPE, g0=ci.G0_SOLAR, rho_b=info["rho_b"], p_b=info["p_b"])
+    oracle.build()
+    times, ref = [], None
+    t_start = time.perf_counter()
+    while not times or (time.perf_counter() - t_start < budget_s and len(times) < 5):
+        t0 = time.perf_counter()
+        ref = oracle.residual(og, U0, Br, want_scale=True)
+        times.append(time.perf_counter() - t0)
+    ncell = int(np.prod(SHAPE))
+    cb = {"value": ncell * len(times) / sum(times), "unit": "cell-updates/s", "cores": 1,
+          "kind": "oracle",
+          "sample": f"{len(times)} full 128x64x128 residual evaluations (FP64 C++, one thread)"}
+    err = {}
+    scale = ref["scale"].reshape(9, -1).max(axis=1)
+    names = ["rho", "mx", "my", "mz", "Bx", "By", "Bz", "E", "psi"]
+    for tag, R in (("fp32", R32), ("fp64", R64)):
+        if R is not None:
+            e = np.abs(R.reshape(9, -1) - ref["R"].reshape(9, -1)).max(axis=1) / scale
+            err[tag] = {n: float(x) for n, x in zip(names, e)}
+    err["metric"] = "max_cells |R - R_oracle| / max_cells (1/V) sum_f |F*_v||S_f| per variable"
+    return cb, err
+
+
+# ---------------------------------------------------------------------------
+# the reference arm: the oracle, timed on the host cores
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    import numpy as np
+
+    import coronal_inputs as ci
+    import oracle
+
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    oracle.build()
+    steps, warmup = args.steps, max(0, args.warmup)
+    # per-step sample: an n_s x 64 x 128 slab problem of the same shell (same
+    # stencil and per-cell work), sized so that warm-up + timed steps stay
+    # within about two minutes of one core
+    probe_shape = (4, SHAPE[1], SHAPE[2])
+    U, info = ci.background(*probe_shape)
+    Br = ci.magnetogram(SHAPE[1], SHAPE[2], seed=2209)
+    og = oracle.Grid(*probe_shape, g0=ci.G0_SOLAR, rho_b=info["rho_b"], p_b=info["p_b"])
+    t0 = time.perf_counter()
+    oracle.residual(og, U, Br)
+    per_cell = (time.perf_counter() - t0) / np.prod(probe_shape)
+    budget = 120.0 / max(1, steps + min(warmup, 3))
+    n_s = int(max(2, min(SHAPE[0], budget / (per_cell * SHAPE[1] * SHAPE[2]))))
+    shape = (n_s, SHAPE[1], SHAPE[2])
+    U, info = ci.background(*shape, r_out=1.0 * (21.5 ** (n_s / SHAPE[0])))
+    og = oracle.Grid(*shape, r_out=21.5 ** (n_s / SHAPE[0]), g0=ci.G0_SOLAR,
+                     rho_b=info["rho_b"], p_b=info["p_b"])
+    for _ in range(min(warmup, 3)):
+        oracle.residual(og, U, Br)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        oracle.residual(og, U, Br)
+    sec = time.perf_counter() - t0
+    ncell = int(np.prod(shape))
+    value = ncell * steps / sec
+    sample = (f"each step: one oracle residual of the innermost {n_s} of the 128 radial planes "
+              f"({n_s}x64x128 cells, same radial spacing), FP64 C++, one thread")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "cell-updates/s",
+        "n_gpus": world, "steps": steps, "warmup": warmup, "ms_per_step": sec * 1e3 / steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cells_per_step": ncell, "parallelism": "cpu x1"},
+        "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gb300(args)
+
+
+if __name__ == "__main__":
+    main()
