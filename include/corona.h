@@ -134,6 +134,33 @@ int crn_residual_vjp(crn_grid* g, const void* U_dev, const void* Rbar_dev, void*
 int crn_pseudo_time_step(crn_grid* g, double* U64_dev, int32_t nsteps, double cfl,
                          double* res_log10_dev, void* stream);
 
+/* One residual evaluation that allocates nothing: the same operator and
+ * kernel as crn_residual, for callers that cannot call cudaMalloc (a host
+ * framework that fixes the device memory budget, a plugin that may not
+ * allocate during a solve, code that must not trigger an allocator's implicit
+ * device synchronisation).  The paper has no counterpart: this is a
+ * deployment variant of the library, not part of the method.
+ * No grid object is needed: *d describes the shell as for crn_grid_create
+ * (d->kernel is ignored; the tiled kernel is used).  Br_dev: FP64 device
+ * array [n_theta][n_phi] read during the call; U_dev, R_dev, norms9_dev,
+ * dtmin_dev as for crn_residual (norms9_dev, dtmin_dev may be NULL).
+ * Scratch (geometry, reduction partials, arrival counter, error word) is one
+ * fixed device array of about 3.6 MB inside the library, held by every GPU
+ * that loads the library until process exit.  Limits: n_r <= 1024,
+ * n_theta <= 1024, n_phi <= 2048 (a multiple of 8), n_theta * n_phi <= 32768;
+ * larger sizes return CRN_E_ARG (nothing is launched).  The first call on a
+ * device, with that device current, resolves the array's address
+ * (cudaGetSymbolAddress) and sets kernel attributes: make it before any
+ * stream capture.  A call whose geometry fields (sizes, precision, radii, g0)
+ * differ from the previous call's rebuilds the geometry on the stream first.
+ * Every call clears the counter and error word it uses and shares the array:
+ * calls that overlap on the GPU race and must be serialised by the caller.
+ * Kernel-detected non-physical states are not reported (no error word is
+ * returned); they show up as non-finite norms.  Calls no cudaMalloc,
+ * cudaFree or other allocating routine.  Asynchronous on `stream`. */
+int crn_residual_static(const crn_grid_desc* d, const double* Br_dev, const void* U_dev,
+                        void* R_dev, double* norms9_dev, double* dtmin_dev, void* stream);
+
 /* Synchronise the stream, then read and clear the grid's device error word.
  * Returns CRN_E_NONPHYSICAL if a kernel saw a non-physical state since the
  * last call (crn_last_bad_cell gives the lowest flagged cell index,

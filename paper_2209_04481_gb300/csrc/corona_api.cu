@@ -230,6 +230,10 @@ int check_ready(const crn_grid* g) {
 
 }  // namespace
 
+namespace crn {
+int report_error(int code, const char* msg) { return fail(code, msg ? msg : ""); }
+}  // namespace crn
+
 extern "C" {
 
 int crn_grid_desc_default(crn_grid_desc* d, int32_t n_r, int32_t n_theta, int32_t n_phi) {

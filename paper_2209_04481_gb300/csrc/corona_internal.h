@@ -65,4 +65,7 @@ size_t tiled_smem_fp32();
 cudaError_t prepare_fp64();
 cudaError_t prepare_fp32();
 
+// record `msg` as the calling thread's last error (crn_last_error); returns code
+int report_error(int code, const char* msg);
+
 }  // namespace crn
