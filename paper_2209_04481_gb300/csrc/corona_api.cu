@@ -278,10 +278,12 @@ int crn_grid_create(const crn_grid_desc* d, crn_grid** out) {
   g->ph32 = make_phys<float>(*d, h.fa, h.fb);
   // tiled launch: radial chunk so that the grid holds a few CTAs per SM
   {
-    const int tt = d->precision == CRN_FP64 ? 4 : 8, tp = 32;
+    const int tt = 8, tp = 32;
     const int64_t ntiles = (int64_t)((d->n_theta + tt - 1) / tt) * ((d->n_phi + tp - 1) / tp);
     int kc = d->n_r;
-    const int64_t target = 2 * 152;
+    // about one wave of resident CTAs on 152 SMs (measured on 128x64x128:
+    // 16 planes per CTA beat 8 and 32)
+    const int64_t target = 243;
     while (kc > 8 && ntiles * ((d->n_r + kc - 1) / kc) < target) kc = (kc + 1) / 2;
     if (const char* env = std::getenv("CRN_KCHUNK")) {  // tuning override
       const int v = std::atoi(env);

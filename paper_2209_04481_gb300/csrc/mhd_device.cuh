@@ -247,8 +247,8 @@ __device__ __forceinline__ void map_column(int& j, int& i, int nt, int np) {
   if (j < 0) { j = -1 - j; i += np / 2; }
   else if (j >= nt) { j = 2 * nt - 1 - j; i += np / 2; }
   j = j < 0 ? 0 : (j >= nt ? nt - 1 : j);
-  i %= np;
-  if (i < 0) i += np;
+  while (i >= np) i -= np;  // i stays within a few periods: no integer division
+  while (i < 0) i += np;
 }
 
 }  // namespace crn

@@ -70,7 +70,9 @@ __device__ __forceinline__ void flag_bad(const Reduce& red, long long cell) {
 
 // Block + grid reduction of 9 sums of squares and one minimum.  Every thread
 // of every CTA calls it once at the end of the kernel.
-template <int NTHREADS>
+// WARP_DONE: the caller has already reduced within each warp (lane 0 holds
+// the warp's sums, every lane the warp's minimum).
+template <int NTHREADS, bool WARP_DONE = false>
 __device__ void reduce_and_finalize(const double (&sum)[NV], double dtmin, const Reduce& red,
                                     double* scratch /* >= (NTHREADS/32) * RED_STRIDE doubles */) {
   constexpr int NW = NTHREADS / 32;
@@ -79,11 +81,13 @@ __device__ void reduce_and_finalize(const double (&sum)[NV], double dtmin, const
 #pragma unroll
   for (int q = 0; q < NV; ++q) v[q] = sum[q];
   v[NV] = dtmin;
+  if (!WARP_DONE) {
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
+    for (int off = 16; off > 0; off >>= 1) {
 #pragma unroll
-    for (int q = 0; q < NV; ++q) v[q] += __shfl_xor_sync(0xffffffffu, v[q], off);
-    v[NV] = fmin(v[NV], __shfl_xor_sync(0xffffffffu, v[NV], off));
+      for (int q = 0; q < NV; ++q) v[q] += __shfl_xor_sync(0xffffffffu, v[q], off);
+      v[NV] = fmin(v[NV], __shfl_xor_sync(0xffffffffu, v[NV], off));
+    }
   }
   __syncthreads();  // scratch may alias buffers still in use
   if (lane == 0) {
@@ -318,32 +322,67 @@ residual_cellwise(Shape sh, Geo<T> g, Phys<T> ph, const double* __restrict__ Br,
 // ---------------------------------------------------------------------------
 // production kernel: radial marching over a (theta, phi) tile
 // ---------------------------------------------------------------------------
+// Thread (jj, ii) owns column (j0 + jj, i0 + ii) of the tile.  Per plane k:
+//   A  the prefetched plane k + 2 (own cell + at most one halo cell per thread)
+//      is recovered to primitives and stored in a 3-plane ring (k, k+1, k+2)
+//   B  the loads of plane k + 3 are issued (they complete during B-E); every
+//      cell of plane k gets its theta and phi slopes once, stored as the lower
+//      and upper face values; the own column gets the r slope of plane k + 1
+//      (registers)
+//   C  every theta and phi face of plane k is evaluated once (Rusanov + GLM)
+//      into shared memory; the r face k + 1/2 stays in registers
+//   E  each cell gathers its six faces, adds gravity and writes R
+// The r face k - 1/2 and the upper r face value of plane k + 1 are carried in
+// registers from one plane to the next.
 template <int TT, int TP>
 struct TileDims {
-  static constexpr int NT = TT * TP;           // threads = own columns
+  static constexpr int NT = TT * TP;                            // threads = own columns
   static constexpr int HT = TT + 4, HP = TP + 4, HC = HT * HP;  // halo'd plane
-  static constexpr int NFR = TT * TP;          // r faces per plane
-  static constexpr int NFT = (TT + 1) * TP;    // theta faces per plane
-  static constexpr int NFP = TT * (TP + 1);    // phi faces per plane
-  static constexpr int NF = NV + 1;            // 9 fluxes + lambda |S|
+  static constexpr int NHALO = HC - NT;                         // halo positions
+  static constexpr int NTV = (TT + 1) * TP;                     // theta faces (rows 0..TT)
+  static constexpr int NPV = TT * (TP + 1);                     // phi faces (cols 0..TP)
+  static constexpr int NF = NV + 1;                             // 9 fluxes + lambda |S|
+  static constexpr int NEXTRA_V = 2 * TP + 2 * TT;              // halo cells needing face values
+  static constexpr int NEXTRA_F = TP + TT;                      // faces beyond the own lower faces
   template <class T>
   static constexpr size_t smem_bytes() {
-    return sizeof(T) * ((size_t)4 * NV * HC + (size_t)NF * (2 * NFR + NFT + NFP));
+    return sizeof(T) * ((size_t)3 * NV * HC + (size_t)2 * NV * (NTV + NPV) +
+                        (size_t)NF * (NTV + NPV));
+  }
+  // halo position h in [0, NHALO) -> halo'd (row, col)
+  __device__ static void halo_rc(int h, int& row, int& col) {
+    if (h < 2 * HP) { row = h / HP; col = h % HP; }
+    else if (h < 4 * HP) { h -= 2 * HP; row = TT + 2 + h / HP; col = h % HP; }
+    else { h -= 4 * HP; row = 2 + h / 4; const int c = h % 4; col = c < 2 ? c : TP + c; }
   }
 };
 
+template <class T>
+__device__ __forceinline__ void load_raw(const T* __restrict__ src, int64_t N, int64_t c, T (&u)[NV]) {
+#pragma unroll
+  for (int v = 0; v < NV; ++v) u[v] = __ldg(src + v * N + c);
+}
+
+// resident CTAs per SM the register allocation is sized for: two FP32 CTAs
+// (16 warps); FP64 CTAs are limited to one by their shared memory anyway
+template <class T> struct MinCtas { static constexpr int value = sizeof(T) == 4 ? 2 : 1; };
+
 template <class T, int LIM, int TT, int TP>
-__global__ void __launch_bounds__(TT * TP)
+__global__ void __launch_bounds__(TT * TP, MinCtas<T>::value)
 residual_tiled(Shape sh, Geo<T> g, Phys<T> ph, const double* __restrict__ Br,
                const T* __restrict__ U, T* __restrict__ R, Reduce red, int kchunk) {
   using D = TileDims<TT, TP>;
-  constexpr int NT = D::NT, HP = D::HP, HC = D::HC;
-  constexpr int NFR = D::NFR, NFT = D::NFT, NFP = D::NFP, NF = D::NF;
+  constexpr int NT = D::NT, HP = D::HP, HC = D::HC, NTV = D::NTV, NPV = D::NPV, NF = D::NF;
+  static_assert(D::NHALO <= NT, "each thread stores at most one halo position");
+  static_assert(D::NEXTRA_F <= NT && NT % 32 == 0, "tile shape");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* ring = reinterpret_cast<T*>(smem_raw);   // [4][NV][HC]
-  T* frb = ring + 4 * NV * HC;                // [2][NF][NFR]
-  T* ftb = frb + 2 * NF * NFR;                // [NF][NFT]
-  T* fpb = ftb + NF * NFT;                    // [NF][NFP]
+  T* ring = reinterpret_cast<T*>(smem_raw);  // [3][NV][HC]   primitives of planes k..k+2
+  T* tvu = ring + 3 * NV * HC;               // [NV][NTV]     theta: upper value of the row below face f
+  T* tvl = tvu + NV * NTV;                   // [NV][NTV]     theta: lower value of the row above face f
+  T* pvu = tvl + NV * NTV;                   // [NV][NPV]     phi: upper value of the col left of face f
+  T* pvl = pvu + NV * NPV;                   // [NV][NPV]     phi: lower value of the col right of face f
+  T* ftb = pvl + NV * NPV;                   // [NF][NTV]     theta face fluxes x area, lambda x area
+  T* fpb = ftb + NF * NTV;                   // [NF][NPV]     phi face fluxes x area, lambda x area
 
   const int nr = sh.nr, nt = sh.nt, np = sh.np;
   const int64_t N = sh.ncell, cs = (int64_t)nt * np;
@@ -355,197 +394,320 @@ residual_tiled(Shape sh, Geo<T> g, Phys<T> ph, const double* __restrict__ Br,
   const int jj = tid / TP, ii = tid % TP;
   const int jo = j0 + jj, io = i0 + ii;
   const bool own = jo < nt && io < np;
-  const int64_t ocol = own ? (int64_t)jo * np + io : 0;
   const int hown = (jj + 2) * HP + (ii + 2);
+  // global column of the own position and of this thread's halo position
+  int64_t c_own, c_halo = 0;
+  int h_halo = -1;
+  {
+    int j = jo, i = io;
+    map_column(j, i, nt, np);
+    c_own = (int64_t)j * np + i;
+    if (tid < D::NHALO) {
+      int row, col;
+      D::halo_rc(tid, row, col);
+      h_halo = row * HP + col;
+      int jh = j0 - 2 + row, ih = i0 - 2 + col;
+      map_column(jh, ih, nt, np);
+      c_halo = (int64_t)jh * np + ih;
+    }
+  }
+  const int64_t ocol = own ? (int64_t)jo * np + io : 0;
+  const T one = (T)1, half = (T)0.5;
 
-  auto slot = [&](int p) -> T* { return ring + ((p + 4) & 3) * (NV * HC); };
+  auto slot = [&](int p) -> T* { return ring + ((p + 3) % 3) * (NV * HC); };
 
-  // load plane p (0 <= p < nr) of the halo'd tile and recover its primitives
-  auto load_plane = [&](int p) {
-    T* dst = slot(p);
+  // raw state of the prefetched plane (own position, halo position)
+  T pf_own[NV], pf_halo[NV];
+  auto prefetch = [&](int p) {
     const T* src = U + (int64_t)p * cs;
-    for (int q = tid; q < HC; q += NT) {
-      int j = j0 - 2 + q / HP, i = i0 - 2 + q % HP;
-      map_column(j, i, nt, np);
-      const int64_t c = (int64_t)j * np + i;
-      T u[NV], w[NV];
+    load_raw(src, N, c_own, pf_own);
+    if (h_halo >= 0) load_raw(src, N, c_halo, pf_halo);
+  };
+  auto store_prefetched = [&](int p) {
+    T* dst = slot(p);
+    T w[NV];
+    recover(pf_own, ph, w);
 #pragma unroll
-      for (int v = 0; v < NV; ++v) u[v] = __ldg(src + v * N + c);
-      recover(u, ph, w);
+    for (int v = 0; v < NV; ++v) dst[v * HC + hown] = w[v];
+    if (h_halo >= 0) {
+      recover(pf_halo, ph, w);
 #pragma unroll
-      for (int v = 0; v < NV; ++v) dst[v * HC + q] = w[v];
+      for (int v = 0; v < NV; ++v) dst[v * HC + h_halo] = w[v];
     }
   };
-  // ghost plane -1 (inner, low-E) or nr (outer) from the adjacent interior plane
-  auto ghost_plane = [&](int p) {
-    const T* srcp = slot(p < 0 ? 0 : nr - 1);
-    T* dst = slot(p);
-    for (int q = tid; q < HC; q += NT) {
-      int j = j0 - 2 + q / HP, i = i0 - 2 + q % HP;
-      map_column(j, i, nt, np);
-      const int64_t c = (int64_t)j * np + i;
+  // outer ghost plane nr from plane nr - 1, own and halo positions
+  auto outer_plane = [&]() {
+    const T* src = slot(nr - 1);
+    T* dst = slot(nr);
+    for (int pass = 0; pass < 2; ++pass) {
+      const int h = pass == 0 ? hown : h_halo;
+      if (h < 0) continue;
+      const int64_t c = pass == 0 ? c_own : c_halo;
       T wi[NV], wg[NV];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) wi[v] = srcp[v * HC + q];
-      if (p < 0)
-        inner_ghost(wi, Br[c], (double)g.rhat[c], (double)g.rhat[cs + c], (double)g.rhat[2 * cs + c],
-                    ph, wg);
-      else
-        outer_ghost(wi, g.rhat[c], g.rhat[cs + c], g.rhat[2 * cs + c], ph, wg);
+      for (int v = 0; v < NV; ++v) wi[v] = src[v * HC + h];
+      outer_ghost(wi, g.rhat[c], g.rhat[cs + c], g.rhat[2 * cs + c], ph, wg);
 #pragma unroll
-      for (int v = 0; v < NV; ++v) dst[v * HC + q] = wg[v];
+      for (int v = 0; v < NV; ++v) dst[v * HC + h] = wg[v];
     }
   };
-  auto put_face = [&](T* buf, int stride, int q, const T (&f)[NV], T la) {
+  auto read_own = [&](const T* pl, T (&w)[NV]) {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) buf[v * stride + q] = f[v];
-    buf[NV * stride + q] = la;
+    for (int v = 0; v < NV; ++v) w[v] = pl[v * HC + hown];
   };
-  auto zero_face = [&](T* buf, int stride, int q) {
+  // r slope of plane p for the own column from planes p-1, p, p+1
+  auto r_values = [&](int p, const T (&wm)[NV], const T (&w0)[NV], const T (&wp)[NV], T (&lo)[NV],
+                      T (&up)[NV]) {
+    const T im = g.inv_dm[p], ip = g.inv_dp[p], hm = g.hm[p], hp = g.hp[p];
 #pragma unroll
-    for (int v = 0; v <= NV; ++v) buf[v * stride + q] = (T)0;
+    for (int v = 0; v < NV; ++v) {
+      const T s = limited_slope<LIM>((w0[v] - wm[v]) * im, (wp[v] - w0[v]) * ip, ph.eps);
+      lo[v] = w0[v] - s * hm;
+      up[v] = w0[v] + s * hp;
+    }
   };
-  // r face between planes kf and kf + 1 for own column -> frb[(kf & 1)]
-  auto r_face = [&](int kf) {
-    T* buf = frb + (kf & 1) * (NF * NFR);
-    if (!own) { zero_face(buf, NFR, tid); return; }
-    T wl[NV], wr[NV];
-    if (kf < 0 || kf >= nr - 1) {
-      const T* a = slot(kf);
-      const T* b = slot(kf + 1);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) { wl[v] = a[v * HC + hown]; wr[v] = b[v * HC + hown]; }
+
+  // ---------------- preamble
+  T rL[NV];          // L state of r face k + 1/2 (upper r value of plane k)
+  T frl[NF];         // flux x area of r face k - 1/2, lambda x area last
+  {
+    // planes k0 and k0 + 1 into the ring
+    for (int p = k0; p <= min(k0 + 1, nr - 1); ++p) {
+      prefetch(p);
+      store_prefetched(p);
+    }
+    __syncthreads();
+    if (k0 + 1 >= nr) outer_plane();
+    __syncthreads();
+    T w0[NV], w1[NV], wm1[NV], wm2[NV];
+    read_own(slot(k0), w0);
+    read_own(slot(k0 + 1), w1);
+    // own column of planes k0 - 1 and k0 - 2 (inner ghost for -1)
+    const int64_t ccol = c_own;
+    if (k0 >= 1) {
+      T u[NV];
+      load_raw(U + (int64_t)(k0 - 1) * cs, N, ccol, u);
+      recover(u, ph, wm1);
     } else {
-      T a[NV], b[NV], c[NV], d[NV];
-      const T *pa = slot(kf - 1), *pb = slot(kf), *pc = slot(kf + 1), *pd = slot(kf + 2);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        a[v] = pa[v * HC + hown]; b[v] = pb[v * HC + hown];
-        c[v] = pc[v * HC + hown]; d[v] = pd[v * HC + hown];
-      }
-      face_states<LIM>(a, b, c, d, g.inv_dm[kf], g.inv_dp[kf], g.hp[kf], g.inv_dm[kf + 1],
-                       g.inv_dp[kf + 1], g.hm[kf + 1], ph.eps, wl, wr);
+      inner_ghost(w0, Br[ccol], (double)g.rhat[ccol], (double)g.rhat[cs + ccol],
+                  (double)g.rhat[2 * cs + ccol], ph, wm1);
     }
-    const T area = g.ra[kf + 1] * g.ar[jo];
-    T f[NV], la;
-    rusanov(wl, wr, g.nr[ocol], g.nr[cs + ocol], g.nr[2 * cs + ocol], area, ph, f, la);
-    put_face(buf, NFR, tid, f, la);
-  };
+    if (k0 >= 2) {
+      T u[NV];
+      load_raw(U + (int64_t)(k0 - 2) * cs, N, ccol, u);
+      recover(u, ph, wm2);
+    } else if (k0 == 1) {
+      T wz[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) wz[v] = wm1[v];  // plane 0
+      inner_ghost(wz, Br[ccol], (double)g.rhat[ccol], (double)g.rhat[cs + ccol],
+                  (double)g.rhat[2 * cs + ccol], ph, wm2);
+    }
+    // r face k0 - 1/2
+    T wl[NV], wr[NV], up0[NV];
+    r_values(k0, wm1, w0, w1, wr, up0);  // lower / upper r values of plane k0
+    if (k0 == 0) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) { wl[v] = wm1[v]; wr[v] = w0[v]; }  // boundary: first order
+    } else {
+      T lo[NV];
+      r_values(k0 - 1, wm2, wm1, w0, lo, wl);
+    }
+    if (own) {
+      T f[NV], la;
+      const T area = g.ra[k0] * g.ar[jo];
+      rusanov(wl, wr, g.nr[ocol], g.nr[cs + ocol], g.nr[2 * cs + ocol], area, ph, f, la);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) frl[v] = f[v];
+      frl[NV] = la;
+    } else {
+#pragma unroll
+      for (int v = 0; v < NF; ++v) frl[v] = (T)0;
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) rL[v] = up0[v];
+    if (k0 + 2 < nr) prefetch(k0 + 2);
+  }
 
-  // ---------------- preamble: planes k0-2 .. k0+1 and the r face k0 - 1/2
-  for (int p = max(k0 - 2, 0); p <= min(k0 + 1, nr - 1); ++p) load_plane(p);
-  __syncthreads();
-  if (k0 - 2 <= -1) { ghost_plane(-1); }
-  if (k0 + 1 >= nr) { ghost_plane(nr); }
-  __syncthreads();
-  r_face(k0 - 1);
-
-  Acc<T> acc;
-  acc.init();
+  T sq[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) sq[v] = (T)0;
   T dtm = (T)INFINITY;
-  const T one = (T)1, half = (T)0.5;
 
   for (int k = k0; k < k1; ++k) {
     // ---- A: plane k + 2 enters the ring
+    if (k + 2 < nr) store_prefetched(k + 2);
     __syncthreads();
-    if (k + 2 < nr) load_plane(k + 2);
-    else if (k + 2 == nr) {
-      // the outer ghost needs plane nr - 1, already in the ring
-      ghost_plane(nr);
+    if (k + 2 == nr) {
+      outer_plane();
+      __syncthreads();
+    }
+    // ---- B: prefetch plane k + 3; face values of plane k; r values of plane k + 1
+    if (k + 3 < nr) prefetch(k + 3);
+    const T* Pk = slot(k);
+    T wc[NV];
+    read_own(Pk, wc);
+    {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const T* q = Pk + v * HC + hown;
+        const T st = limited_slope<LIM>(wc[v] - q[-HP], q[HP] - wc[v], ph.eps);
+        tvl[v * NTV + jj * TP + ii] = wc[v] - half * st;
+        tvu[v * NTV + (jj + 1) * TP + ii] = wc[v] + half * st;
+        const T sp = limited_slope<LIM>(wc[v] - q[-1], q[1] - wc[v], ph.eps);
+        pvl[v * NPV + jj * (TP + 1) + ii] = wc[v] - half * sp;
+        pvu[v * NPV + jj * (TP + 1) + ii + 1] = wc[v] + half * sp;
+      }
+      // halo cells whose face values the tile's boundary faces need
+      for (int e = tid; e < D::NEXTRA_V; e += NT) {
+        int hrow, hcol, dstep, idx;
+        T* dst;
+        if (e < TP) {                 // theta row -1: upper value -> face 0
+          hrow = 1; hcol = e + 2; dstep = HP; dst = tvu; idx = e;
+        } else if (e < 2 * TP) {      // theta row TT: lower value -> face TT
+          hrow = TT + 2; hcol = e - TP + 2; dstep = HP; dst = tvl; idx = TT * TP + (e - TP);
+        } else if (e < 2 * TP + TT) { // phi col -1 of row r: upper value -> face 0
+          const int r = e - 2 * TP;
+          hrow = r + 2; hcol = 1; dstep = 1; dst = pvu; idx = r * (TP + 1);
+        } else {                      // phi col TP of row r: lower value -> face TP
+          const int r = e - 2 * TP - TT;
+          hrow = r + 2; hcol = TP + 2; dstep = 1; dst = pvl; idx = r * (TP + 1) + TP;
+        }
+        const bool upper = (dst == tvu) || (dst == pvu);
+        const int nstride = (dst == tvu || dst == tvl) ? NTV : NPV;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const T* q = Pk + v * HC + hrow * HP + hcol;
+          const T w = q[0];
+          const T s = limited_slope<LIM>(w - q[-dstep], q[dstep] - w, ph.eps);
+          dst[v * nstride + idx] = upper ? w + half * s : w - half * s;
+        }
+      }
+    }
+    T rR[NV], rLn[NV];
+    if (k + 1 < nr) {
+      T w1[NV], w2[NV];
+      read_own(slot(k + 1), w1);
+      read_own(slot(k + 2), w2);
+      r_values(k + 1, wc, w1, w2, rR, rLn);
     }
     __syncthreads();
-    // ---- C: every face of plane k, once
-    for (int q = tid; q < NFR + NFT + NFP; q += NT) {
-      if (q < NFR) {
-        if (q == tid) r_face(k);  // q == tid for the r faces (NFR == NT)
-      } else if (q < NFR + NFT) {
-        const int qt = q - NFR;
-        const int frow = qt / TP, col = qt % TP;
-        const int jf = j0 + frow, ic = i0 + col;
-        if (jf <= 0 || jf >= nt || ic >= np) { zero_face(ftb, NFT, qt); continue; }
-        const T* pl = slot(k);
-        T a[NV], b[NV], c[NV], d[NV], wl[NV], wr[NV];
-        const int h0 = frow * HP + col + 2;
+    // ---- C: faces of plane k
+    {
+      const int64_t ts = (int64_t)(nt + 1) * np;
+      const T rbk = g.rb[k];
+      // theta faces: own lower face (row jj) and, for the extra threads, face TT
+      for (int q = tid; q < NTV; q += NT) {
+        const int f = q / TP, col = q % TP;
+        const int jf = j0 + f, ic = i0 + col;
+        if (jf <= 0 || jf >= nt || ic >= np) {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          a[v] = pl[v * HC + h0]; b[v] = pl[v * HC + h0 + HP];
-          c[v] = pl[v * HC + h0 + 2 * HP]; d[v] = pl[v * HC + h0 + 3 * HP];
+          for (int v = 0; v < NF; ++v) ftb[v * NTV + q] = (T)0;
+          continue;
         }
-        face_states<LIM>(a, b, c, d, one, one, half, one, one, half, ph.eps, wl, wr);
+        T wl[NV], wr[NV], fl[NV], la;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) { wl[v] = tvu[v * NTV + q]; wr[v] = tvl[v * NTV + q]; }
         const int64_t fc = (int64_t)jf * np + ic;
-        const int64_t ts = (int64_t)(nt + 1) * np;
-        const T area = g.rb[k] * g.at[jf];
-        T f[NV], la;
-        rusanov(wl, wr, g.nth[fc], g.nth[ts + fc], g.nth[2 * ts + fc], area, ph, f, la);
-        put_face(ftb, NFT, qt, f, la);
-      } else {
-        const int qp = q - NFR - NFT;
-        const int row = qp / (TP + 1), fcol = qp % (TP + 1);
-        const int jr = j0 + row, ifc = i0 + fcol;
-        if (jr >= nt || ifc > np) { zero_face(fpb, NFP, qp); continue; }
-        const T* pl = slot(k);
-        T a[NV], b[NV], c[NV], d[NV], wl[NV], wr[NV];
-        const int h0 = (row + 2) * HP + fcol;
+        rusanov(wl, wr, g.nth[fc], g.nth[ts + fc], g.nth[2 * ts + fc], rbk * g.at[jf], ph, fl, la);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          a[v] = pl[v * HC + h0]; b[v] = pl[v * HC + h0 + 1];
-          c[v] = pl[v * HC + h0 + 2]; d[v] = pl[v * HC + h0 + 3];
-        }
-        face_states<LIM>(a, b, c, d, one, one, half, one, one, half, ph.eps, wl, wr);
-        const int iw = ifc == np ? 0 : ifc;
-        const T area = g.rb[k] * g.dtheta;
-        T f[NV], la;
-        rusanov(wl, wr, g.nph[iw], g.nph[np + iw], (T)0, area, ph, f, la);
-        put_face(fpb, NFP, qp, f, la);
+        for (int v = 0; v < NV; ++v) ftb[v * NTV + q] = fl[v];
+        ftb[NV * NTV + q] = la;
       }
+      // phi faces: own lower face (col ii) and, for the extra threads, face TP
+      for (int q = tid; q < NPV; q += NT) {
+        // own threads take q = jj * (TP + 1) + ii; the extras the faces f = TP
+        int row, f;
+        if (q < NT) { row = q / TP; f = q % TP; }
+        else { row = q - NT; f = TP; }
+        const int qq = row * (TP + 1) + f;
+        const int jr = j0 + row, ifc = i0 + f;
+        if (jr >= nt || ifc > np || (f == TP && ifc - 1 >= np)) {
+#pragma unroll
+          for (int v = 0; v < NF; ++v) fpb[v * NPV + qq] = (T)0;
+          continue;
+        }
+        T wl[NV], wr[NV], fl[NV], la;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) { wl[v] = pvu[v * NPV + qq]; wr[v] = pvl[v * NPV + qq]; }
+        const int iw = ifc == np ? 0 : ifc;
+        rusanov(wl, wr, g.nph[iw], g.nph[np + iw], (T)0, rbk * g.dtheta, ph, fl, la);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) fpb[v * NPV + qq] = fl[v];
+        fpb[NV * NPV + qq] = la;
+      }
+    }
+    // r face k + 1/2 (own column, registers)
+    T fru[NF];
+    if (own) {
+      T wl[NV], wr[NV], fl[NV], la;
+      if (k + 1 < nr) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) { wl[v] = rL[v]; wr[v] = rR[v]; }
+      } else {  // outer boundary face: first order, interior | ghost
+        const T* pg = slot(nr);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) { wl[v] = wc[v]; wr[v] = pg[v * HC + hown]; }
+      }
+      rusanov(wl, wr, g.nr[ocol], g.nr[cs + ocol], g.nr[2 * cs + ocol], g.ra[k + 1] * g.ar[jo], ph,
+              fl, la);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) fru[v] = fl[v];
+      fru[NV] = la;
     }
     __syncthreads();
     // ---- E: gather the six faces of cell (k, jo, io)
     if (own) {
-      const T* lo = frb + ((k - 1) & 1) * (NF * NFR);
-      const T* hi = frb + (k & 1) * (NF * NFR);
       const int tl = jj * TP + ii, tu = tl + TP;
       const int pl = jj * (TP + 1) + ii, pu = pl + 1;
       T r[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v)
-        r[v] = (lo[v * NFR + tid] - hi[v * NFR + tid]) + (ftb[v * NFT + tl] - ftb[v * NFT + tu])
-               + (fpb[v * NFP + pl] - fpb[v * NFP + pu]);
-      const T lam = (lo[NV * NFR + tid] + hi[NV * NFR + tid]) + (ftb[NV * NFT + tl] + ftb[NV * NFT + tu])
-                    + (fpb[NV * NFP + pl] + fpb[NV * NFP + pu]);
+        r[v] = (frl[v] - fru[v]) + (ftb[v * NTV + tl] - ftb[v * NTV + tu]) +
+               (fpb[v * NPV + pl] - fpb[v * NPV + pu]);
+      const T lam = (frl[NV] + fru[NV]) + (ftb[NV * NTV + tl] + ftb[NV * NTV + tu]) +
+                    (fpb[NV * NPV + pl] + fpb[NV * NPV + pu]);
       const T vol = g.rv[k] * g.av[jo];
       const T ivol = one / vol;
 #pragma unroll
       for (int v = 0; v < NV; ++v) r[v] *= ivol;
-      const T* wc = slot(k);
-      const T rho = wc[hown], vx = wc[HC + hown], vy = wc[2 * HC + hown], vz = wc[3 * HC + hown];
       const T gk = -g.grav[k];
       const T gx = gk * g.rhat[ocol], gy = gk * g.rhat[cs + ocol], gz = gk * g.rhat[2 * cs + ocol];
-      r[1] += rho * gx;
-      r[2] += rho * gy;
-      r[3] += rho * gz;
-      r[7] += rho * (vx * gx + vy * gy + vz * gz);
+      r[1] += wc[0] * gx;
+      r[2] += wc[0] * gy;
+      r[3] += wc[0] * gz;
+      r[7] += wc[0] * (wc[1] * gx + wc[2] * gy + wc[3] * gz);
       const int64_t cell = (int64_t)k * cs + ocol;
       T chk = (T)0;
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         R[v * N + cell] = r[v];
-        acc.add(v, r[v]);
-        chk += r[v] * r[v];
+        const T r2 = r[v] * r[v];
+        sq[v] += r2;
+        chk += r2;
       }
       const T dtc = vol / lam;
       dtm = dtc < dtm ? dtc : dtm;
-      const T pc = wc[7 * HC + hown];
-      if (!(rho > (T)0) || !(pc > (T)0) || !(chk == chk) || chk > (T)1e300 * (T)1e300)
-        flag_bad(red, cell);
+      if (!(wc[0] > (T)0) || !(wc[7] > (T)0) || !(fabs(chk) < (T)INFINITY)) flag_bad(red, cell);
+#pragma unroll
+      for (int v = 0; v < NF; ++v) frl[v] = fru[v];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) rL[v] = rLn[v];
     }
   }
-  // ---------------- reductions
+  // ---------------- reductions: warp tree in T, then FP64 across warps and CTAs
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) sq[v] += __shfl_xor_sync(0xffffffffu, sq[v], off);
+    const T o = __shfl_xor_sync(0xffffffffu, dtm, off);
+    dtm = o < dtm ? o : dtm;
+  }
   double tot[NV];
 #pragma unroll
-  for (int v = 0; v < NV; ++v) tot[v] = acc.total(v);
+  for (int v = 0; v < NV; ++v) tot[v] = (threadIdx.x & 31) == 0 ? (double)sq[v] : 0.0;
   double* scratch = reinterpret_cast<double*>(smem_raw);
-  reduce_and_finalize<NT>(tot, (double)dtm, red, scratch);
+  reduce_and_finalize<NT, true>(tot, (double)dtm, red, scratch);
 }
 
 }  // namespace crn

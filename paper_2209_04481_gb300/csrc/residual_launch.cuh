@@ -9,7 +9,7 @@
 namespace crn {
 
 template <class T> struct TileFor;
-template <> struct TileFor<double> { static constexpr int TT = 4, TP = 32; };
+template <> struct TileFor<double> { static constexpr int TT = 8, TP = 32; };
 template <> struct TileFor<float> { static constexpr int TT = 8, TP = 32; };
 
 template <class T> const Geo<T>& geo_of(const crn_grid* g);

@@ -217,7 +217,7 @@ crn::Phys<T> phys_static(const crn_grid_desc& d) {
 }
 
 template <class T> struct StaticTile;
-template <> struct StaticTile<double> { static constexpr int TT = 4, TP = 32; };
+template <> struct StaticTile<double> { static constexpr int TT = 8, TP = 32; };
 template <> struct StaticTile<float> { static constexpr int TT = 8, TP = 32; };
 
 template <class T>
@@ -251,7 +251,7 @@ int run(const crn_grid_desc& d, unsigned char* base, const double* Br, const voi
   sh.ncell = (int64_t)d.n_r * d.n_theta * d.n_phi;
   const int ntiles = ((sh.nt + TT - 1) / TT) * ((sh.np + TP - 1) / TP);
   int kc = sh.nr;
-  while (kc > 8 && ntiles * ((sh.nr + kc - 1) / kc) < 2 * 152) kc = (kc + 1) / 2;
+  while (kc > 8 && ntiles * ((sh.nr + kc - 1) / kc) < 243) kc = (kc + 1) / 2;
   while ((int64_t)ntiles * ((sh.nr + kc - 1) / kc) > kMaxBlocks) kc *= 2;
   const int nch = (sh.nr + kc - 1) / kc;
   crn::Reduce red;
