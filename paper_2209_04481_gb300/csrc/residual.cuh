@@ -344,10 +344,12 @@ struct TileDims {
   static constexpr int NF = NV + 1;                             // 9 fluxes + lambda |S|
   static constexpr int NEXTRA_V = 2 * TP + 2 * TT;              // halo cells needing face values
   static constexpr int NEXTRA_F = TP + TT;                      // faces beyond the own lower faces
+  // per-CTA geometry staged once: theta-face normals, phi-face normals, own
+  // r-face normals, own radial unit vectors, theta factors of the areas/volumes
+  static constexpr int NGEO = 3 * NTV + 2 * (TP + 1) + 6 * NT + (TT + 1) + 2 * TT;
   template <class T>
   static constexpr size_t smem_bytes() {
-    return sizeof(T) * ((size_t)3 * NV * HC + (size_t)2 * NV * (NTV + NPV) +
-                        (size_t)NF * (NTV + NPV));
+    return sizeof(T) * ((size_t)3 * NV * HC + (size_t)2 * NV * (NTV + NPV) + (size_t)NGEO);
   }
   // halo position h in [0, NHALO) -> halo'd (row, col)
   __device__ static void halo_rc(int h, int& row, int& col) {
@@ -381,8 +383,21 @@ residual_tiled(Shape sh, Geo<T> g, Phys<T> ph, const double* __restrict__ Br,
   T* tvl = tvu + NV * NTV;                   // [NV][NTV]     theta: lower value of the row above face f
   T* pvu = tvl + NV * NTV;                   // [NV][NPV]     phi: upper value of the col left of face f
   T* pvl = pvu + NV * NPV;                   // [NV][NPV]     phi: lower value of the col right of face f
-  T* ftb = pvl + NV * NPV;                   // [NF][NTV]     theta face fluxes x area, lambda x area
-  T* fpb = ftb + NF * NTV;                   // [NF][NPV]     phi face fluxes x area, lambda x area
+  // face fluxes x area overwrite the face values they were computed from (each
+  // face is read and written by one thread): flux v of theta face f in
+  // tvu[v][f], its lambda x area in tvl[0][f]; likewise phi faces in pvu / pvl
+  T* ftb = tvu;
+  T* fpb = pvu;
+  T* ftl = tvl;                              // lambda x area of theta faces
+  T* fpl = pvl;                              // lambda x area of phi faces
+  T* gs = pvl + NV * NPV;                    // per-CTA geometry
+  T* s_nth = gs;                             // [3][NTV]
+  T* s_nph = s_nth + 3 * NTV;                // [2][TP + 1]
+  T* s_nr = s_nph + 2 * (TP + 1);            // [3][NT]
+  T* s_rh = s_nr + 3 * NT;                   // [3][NT]
+  T* s_at = s_rh + 3 * NT;                   // [TT + 1]
+  T* s_ar = s_at + (TT + 1);                 // [TT]
+  T* s_av = s_ar + TT;                       // [TT]
 
   const int nr = sh.nr, nt = sh.nt, np = sh.np;
   const int64_t N = sh.ncell, cs = (int64_t)nt * np;
@@ -413,6 +428,34 @@ residual_tiled(Shape sh, Geo<T> g, Phys<T> ph, const double* __restrict__ Br,
   }
   const int64_t ocol = own ? (int64_t)jo * np + io : 0;
   const T one = (T)1, half = (T)0.5;
+  {
+    const int64_t ts = (int64_t)(nt + 1) * np;
+    for (int q = tid; q < NTV; q += NT) {
+      const int f = q / TP, col = q % TP;
+      const int jf = min(j0 + f, nt), ic = min(i0 + col, np - 1);
+      const int64_t fc = (int64_t)jf * np + ic;
+      s_nth[q] = g.nth[fc];
+      s_nth[NTV + q] = g.nth[ts + fc];
+      s_nth[2 * NTV + q] = g.nth[2 * ts + fc];
+    }
+    for (int q = tid; q <= TP; q += NT) {
+      int ic = i0 + q;
+      ic = ic >= np ? ic - np : ic;
+      s_nph[q] = g.nph[ic];
+      s_nph[TP + 1 + q] = g.nph[np + ic];
+    }
+    s_nr[tid] = g.nr[ocol];
+    s_nr[NT + tid] = g.nr[cs + ocol];
+    s_nr[2 * NT + tid] = g.nr[2 * cs + ocol];
+    s_rh[tid] = g.rhat[c_own];
+    s_rh[NT + tid] = g.rhat[cs + c_own];
+    s_rh[2 * NT + tid] = g.rhat[2 * cs + c_own];
+    if (tid <= TT) s_at[tid] = g.at[min(j0 + tid, nt)];
+    if (tid < TT) {
+      s_ar[tid] = g.ar[min(j0 + tid, nt - 1)];
+      s_av[tid] = g.av[min(j0 + tid, nt - 1)];
+    }
+  }
 
   auto slot = [&](int p) -> T* { return ring + ((p + 3) % 3) * (NV * HC); };
 
@@ -515,8 +558,8 @@ residual_tiled(Shape sh, Geo<T> g, Phys<T> ph, const double* __restrict__ Br,
     }
     if (own) {
       T f[NV], la;
-      const T area = g.ra[k0] * g.ar[jo];
-      rusanov(wl, wr, g.nr[ocol], g.nr[cs + ocol], g.nr[2 * cs + ocol], area, ph, f, la);
+      const T area = g.ra[k0] * s_ar[jj];
+      rusanov(wl, wr, s_nr[tid], s_nr[NT + tid], s_nr[2 * NT + tid], area, ph, f, la);
 #pragma unroll
       for (int v = 0; v < NV; ++v) frl[v] = f[v];
       frl[NV] = la;
@@ -594,48 +637,45 @@ residual_tiled(Shape sh, Geo<T> g, Phys<T> ph, const double* __restrict__ Br,
     __syncthreads();
     // ---- C: faces of plane k
     {
-      const int64_t ts = (int64_t)(nt + 1) * np;
       const T rbk = g.rb[k];
-      // theta faces: own lower face (row jj) and, for the extra threads, face TT
-      for (int q = tid; q < NTV; q += NT) {
+      auto theta_face = [&](int q) {
         const int f = q / TP, col = q % TP;
         const int jf = j0 + f, ic = i0 + col;
-        if (jf <= 0 || jf >= nt || ic >= np) {
+        if (jf <= 0 || jf >= nt || ic >= np) {  // poles, ragged rows / columns
 #pragma unroll
-          for (int v = 0; v < NF; ++v) ftb[v * NTV + q] = (T)0;
-          continue;
+          for (int v = 0; v < NV; ++v) ftb[v * NTV + q] = (T)0;
+          ftl[q] = (T)0;
+          return;
         }
         T wl[NV], wr[NV], fl[NV], la;
 #pragma unroll
         for (int v = 0; v < NV; ++v) { wl[v] = tvu[v * NTV + q]; wr[v] = tvl[v * NTV + q]; }
-        const int64_t fc = (int64_t)jf * np + ic;
-        rusanov(wl, wr, g.nth[fc], g.nth[ts + fc], g.nth[2 * ts + fc], rbk * g.at[jf], ph, fl, la);
+        rusanov(wl, wr, s_nth[q], s_nth[NTV + q], s_nth[2 * NTV + q], rbk * s_at[f], ph, fl, la);
 #pragma unroll
         for (int v = 0; v < NV; ++v) ftb[v * NTV + q] = fl[v];
-        ftb[NV * NTV + q] = la;
-      }
-      // phi faces: own lower face (col ii) and, for the extra threads, face TP
-      for (int q = tid; q < NPV; q += NT) {
-        // own threads take q = jj * (TP + 1) + ii; the extras the faces f = TP
-        int row, f;
-        if (q < NT) { row = q / TP; f = q % TP; }
-        else { row = q - NT; f = TP; }
+        ftl[q] = la;
+      };
+      auto phi_face = [&](int row, int f) {
         const int qq = row * (TP + 1) + f;
         const int jr = j0 + row, ifc = i0 + f;
         if (jr >= nt || ifc > np || (f == TP && ifc - 1 >= np)) {
 #pragma unroll
-          for (int v = 0; v < NF; ++v) fpb[v * NPV + qq] = (T)0;
-          continue;
+          for (int v = 0; v < NV; ++v) fpb[v * NPV + qq] = (T)0;
+          fpl[qq] = (T)0;
+          return;
         }
         T wl[NV], wr[NV], fl[NV], la;
 #pragma unroll
         for (int v = 0; v < NV; ++v) { wl[v] = pvu[v * NPV + qq]; wr[v] = pvl[v * NPV + qq]; }
-        const int iw = ifc == np ? 0 : ifc;
-        rusanov(wl, wr, g.nph[iw], g.nph[np + iw], (T)0, rbk * g.dtheta, ph, fl, la);
+        rusanov(wl, wr, s_nph[f], s_nph[TP + 1 + f], (T)0, rbk * g.dtheta, ph, fl, la);
 #pragma unroll
         for (int v = 0; v < NV; ++v) fpb[v * NPV + qq] = fl[v];
-        fpb[NV * NPV + qq] = la;
-      }
+        fpl[qq] = la;
+      };
+      theta_face(tid);                      // own lower theta face (row jj)
+      phi_face(jj, ii);                     // own lower phi face (col ii)
+      if (tid < TP) theta_face(NT + tid);   // faces of row TT: warp 0
+      if (tid >= 32 && tid < 32 + TT) phi_face(tid - 32, TP);  // faces of col TP: warp 1
     }
     // r face k + 1/2 (own column, registers)
     T fru[NF];
@@ -649,7 +689,7 @@ residual_tiled(Shape sh, Geo<T> g, Phys<T> ph, const double* __restrict__ Br,
 #pragma unroll
         for (int v = 0; v < NV; ++v) { wl[v] = wc[v]; wr[v] = pg[v * HC + hown]; }
       }
-      rusanov(wl, wr, g.nr[ocol], g.nr[cs + ocol], g.nr[2 * cs + ocol], g.ra[k + 1] * g.ar[jo], ph,
+      rusanov(wl, wr, s_nr[tid], s_nr[NT + tid], s_nr[2 * NT + tid], g.ra[k + 1] * s_ar[jj], ph,
               fl, la);
 #pragma unroll
       for (int v = 0; v < NV; ++v) fru[v] = fl[v];
@@ -665,14 +705,13 @@ residual_tiled(Shape sh, Geo<T> g, Phys<T> ph, const double* __restrict__ Br,
       for (int v = 0; v < NV; ++v)
         r[v] = (frl[v] - fru[v]) + (ftb[v * NTV + tl] - ftb[v * NTV + tu]) +
                (fpb[v * NPV + pl] - fpb[v * NPV + pu]);
-      const T lam = (frl[NV] + fru[NV]) + (ftb[NV * NTV + tl] + ftb[NV * NTV + tu]) +
-                    (fpb[NV * NPV + pl] + fpb[NV * NPV + pu]);
-      const T vol = g.rv[k] * g.av[jo];
+      const T lam = (frl[NV] + fru[NV]) + (ftl[tl] + ftl[tu]) + (fpl[pl] + fpl[pu]);
+      const T vol = g.rv[k] * s_av[jj];
       const T ivol = one / vol;
 #pragma unroll
       for (int v = 0; v < NV; ++v) r[v] *= ivol;
       const T gk = -g.grav[k];
-      const T gx = gk * g.rhat[ocol], gy = gk * g.rhat[cs + ocol], gz = gk * g.rhat[2 * cs + ocol];
+      const T gx = gk * s_rh[tid], gy = gk * s_rh[NT + tid], gz = gk * s_rh[2 * NT + tid];
       r[1] += wc[0] * gx;
       r[2] += wc[0] * gy;
       r[3] += wc[0] * gz;
