@@ -276,15 +276,18 @@ int crn_grid_create(const crn_grid_desc* d, crn_grid** out) {
   const HostGeo h = build_geometry(*d);
   g->ph64 = make_phys<double>(*d, h.fa, h.fb);
   g->ph32 = make_phys<float>(*d, h.fa, h.fb);
-  // tiled launch: radial chunk so that the grid holds a few CTAs per SM
+  // opt the kernels in to their shared memory, then size the tiled launch:
+  // radial chunk such that all CTAs fit in one wave of resident CTAs
+  e = d->precision == CRN_FP64 ? crn::prepare_fp64() : crn::prepare_fp32();
+  if (e != cudaSuccess) { delete g; return cuda_fail(e, "kernel attributes"); }
   {
     const int tt = 8, tp = 32;
     const int64_t ntiles = (int64_t)((d->n_theta + tt - 1) / tt) * ((d->n_phi + tp - 1) / tp);
-    int kc = d->n_r;
-    // about one wave of resident CTAs on 152 SMs (measured on 128x64x128:
-    // 16 planes per CTA beat 8 and 32)
-    const int64_t target = 243;
-    while (kc > 8 && ntiles * ((d->n_r + kc - 1) / kc) < target) kc = (kc + 1) / 2;
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, g->device);
+    const int per_sm = d->precision == CRN_FP64 ? crn::tiled_ctas_per_sm_fp64(d->limiter)
+                                                 : crn::tiled_ctas_per_sm_fp32(d->limiter);
+    int kc = crn::choose_kchunk(d->n_r, ntiles, (long long)std::max(nsm, 1) * std::max(per_sm, 1));
     if (const char* env = std::getenv("CRN_KCHUNK")) {  // tuning override
       const int v = std::atoi(env);
       if (v >= 1) kc = v;
@@ -320,8 +323,7 @@ int crn_grid_create(const crn_grid_desc* d, crn_grid** out) {
   cudaMemset(g->stats, 0, 32 * sizeof(double));
   cudaMemset(g->err_flags, 0, sizeof(unsigned int));
   cudaMemset(g->err_cell, 0xff, sizeof(unsigned long long));
-  e = d->precision == CRN_FP64 ? crn::prepare_fp64() : crn::prepare_fp32();
-  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  e = cudaDeviceSynchronize();
   if (e != cudaSuccess) { free_grid(g); return cuda_fail(e, "grid set-up"); }
   *out = g;
   return CRN_OK;

@@ -68,4 +68,20 @@ cudaError_t prepare_fp32();
 // record `msg` as the calling thread's last error (crn_last_error); returns code
 int report_error(int code, const char* msg);
 
+// resident CTAs per SM of the tiled kernel for this precision and limiter
+// (after prepare_*), 0 on error
+int tiled_ctas_per_sm_fp64(int limiter);
+int tiled_ctas_per_sm_fp32(int limiter);
+
+// Radial planes per CTA of the tiled kernel: the largest chunk count whose
+// CTAs all fit in one wave of `slots` resident CTAs (fewer planes per CTA
+// only add preamble work), at least 4 planes per CTA.
+inline int choose_kchunk(int nr, long long ntiles, long long slots) {
+  if (ntiles <= 0 || slots <= 0 || ntiles >= slots) return nr;
+  long long nch = slots / ntiles;
+  if (nch > nr) nch = nr;
+  int kc = (int)((nr + nch - 1) / nch);
+  return kc < 4 ? (nr < 4 ? nr : 4) : kc;
+}
+
 }  // namespace crn

@@ -514,6 +514,12 @@ residual_tiled(Shape sh, Geo<T> g, Phys<T> ph, const double* __restrict__ Br,
   T rL[NV];          // L state of r face k + 1/2 (upper r value of plane k)
   T frl[NF];         // flux x area of r face k - 1/2, lambda x area last
   {
+    // own column of planes k0 - 1 and k0 - 2 (loads issued first so that they
+    // overlap with those of planes k0 and k0 + 1)
+    const int64_t ccol = c_own;
+    T um1[NV], um2[NV];
+    if (k0 >= 1) load_raw(U + (int64_t)(k0 - 1) * cs, N, ccol, um1);
+    if (k0 >= 2) load_raw(U + (int64_t)(k0 - 2) * cs, N, ccol, um2);
     // planes k0 and k0 + 1 into the ring
     for (int p = k0; p <= min(k0 + 1, nr - 1); ++p) {
       prefetch(p);
@@ -525,20 +531,15 @@ residual_tiled(Shape sh, Geo<T> g, Phys<T> ph, const double* __restrict__ Br,
     T w0[NV], w1[NV], wm1[NV], wm2[NV];
     read_own(slot(k0), w0);
     read_own(slot(k0 + 1), w1);
-    // own column of planes k0 - 1 and k0 - 2 (inner ghost for -1)
-    const int64_t ccol = c_own;
+    // inner ghost for plane -1
     if (k0 >= 1) {
-      T u[NV];
-      load_raw(U + (int64_t)(k0 - 1) * cs, N, ccol, u);
-      recover(u, ph, wm1);
+      recover(um1, ph, wm1);
     } else {
       inner_ghost(w0, Br[ccol], (double)g.rhat[ccol], (double)g.rhat[cs + ccol],
                   (double)g.rhat[2 * cs + ccol], ph, wm1);
     }
     if (k0 >= 2) {
-      T u[NV];
-      load_raw(U + (int64_t)(k0 - 2) * cs, N, ccol, u);
-      recover(u, ph, wm2);
+      recover(um2, ph, wm2);
     } else if (k0 == 1) {
       T wz[NV];
 #pragma unroll

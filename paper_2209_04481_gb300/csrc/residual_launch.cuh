@@ -80,6 +80,21 @@ cudaError_t prepare_t() {
 }
 
 template <class T>
+int tiled_ctas_t(int limiter) {
+  constexpr int TT = TileFor<T>::TT, TP = TileFor<T>::TP;
+  const size_t smem = TileDims<TT, TP>::template smem_bytes<T>();
+  int n = 0;
+  cudaError_t e;
+  if (limiter == CRN_LIM_NONE)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, residual_tiled<T, 0, TT, TP>, TT * TP, smem);
+  else if (limiter == CRN_LIM_MINMOD)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, residual_tiled<T, 1, TT, TP>, TT * TP, smem);
+  else
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, residual_tiled<T, 2, TT, TP>, TT * TP, smem);
+  return e == cudaSuccess ? n : 0;
+}
+
+template <class T>
 size_t tiled_smem_t() {
   using D = TileDims<TileFor<T>::TT, TileFor<T>::TP>;
   return D::template smem_bytes<T>();

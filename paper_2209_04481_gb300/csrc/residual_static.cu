@@ -250,8 +250,13 @@ int run(const crn_grid_desc& d, unsigned char* base, const double* Br, const voi
   sh.np = d.n_phi;
   sh.ncell = (int64_t)d.n_r * d.n_theta * d.n_phi;
   const int ntiles = ((sh.nt + TT - 1) / TT) * ((sh.np + TP - 1) / TP);
-  int kc = sh.nr;
-  while (kc > 8 && ntiles * ((sh.nr + kc - 1) / kc) < 243) kc = (kc + 1) / 2;
+  int nsm = 0, per_sm = 0;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, crn::residual_tiled<T, 2, TT, TP>, TT * TP,
+                                                crn::TileDims<TT, TP>::template smem_bytes<T>());
+  int kc = crn::choose_kchunk(sh.nr, ntiles, (long long)std::max(nsm, 1) * std::max(per_sm, 1));
   while ((int64_t)ntiles * ((sh.nr + kc - 1) / kc) > kMaxBlocks) kc *= 2;
   const int nch = (sh.nr + kc - 1) / kc;
   crn::Reduce red;
