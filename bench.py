@@ -347,6 +347,37 @@ def run_gb300(args):
     del graph
     g64.close()
 
+    # ---- residual VJP on the 64 x 32 x 64 perturbed shell (adjoint workload)
+    vjp = {}
+    wv = ci.workload("shell64")
+    nv = int(np.prod(wv["shape"]))
+    for precision in ("fp64", "fp32"):
+        gv = pg.Grid(*wv["shape"], precision=precision, p_b=wv["p_b"])
+        gv.set_inner_boundary(torch.from_numpy(wv["Br"]).to(device))
+        dtv = torch.float64 if precision == "fp64" else torch.float32
+        Uv = torch.from_numpy(wv["U"]).to(device, dtv)
+        Rbv = torch.from_numpy(ci.cotangent(wv["U"].shape, seed=4)).to(device, dtv)
+        Ubv = torch.empty_like(Uv)
+        Brbv = torch.empty(wv["shape"][1:], dtype=torch.float64, device=device)
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                gv.residual_vjp(Uv, Rbv, Ubv, Brbv, stream=stream)
+        stream.synchronize()
+        nrep = 20 if precision == "fp64" else 50
+        v0 = torch.cuda.Event(enable_timing=True)
+        v1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            v0.record(stream)
+            for _ in range(nrep):
+                gv.residual_vjp(Uv, Rbv, Ubv, Brbv, stream=stream)
+            v1.record(stream)
+        torch.cuda.synchronize(device)
+        ms = v0.elapsed_time(v1) / nrep
+        vjp[precision] = {"ms_per_vjp": ms, "cells_per_s": nv / (ms / 1e3),
+                          "launches_per_vjp": gv.last_launch_count}
+        gv.close()
+    vjp["workload"] = "64x32x64 shell, dipole, 1% perturbation (seed 3), N(0,1) cotangent (seed 4)"
+
     result = {
         "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
         "steps": steps, "warmup": warmup, "ms_per_step": sec_max * 1e3 / steps,
@@ -365,6 +396,7 @@ def run_gb300(args):
         "clocks": clocks.summary(),
         "fp64": fp64,
         "pseudo_time_step": pts,
+        "vjp": vjp,
     }
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

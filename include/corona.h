@@ -117,9 +117,15 @@ int crn_set_inner_boundary(crn_grid* g, const double* Br_dev, void* stream);
 int crn_residual(crn_grid* g, const void* U_dev, void* R_dev, double* norms9_dev,
                  double* dtmin_dev, void* stream);
 
-/* Vector-Jacobian product of the residual: Ubar = (dR/dU)^T Rbar (same layout
- * and precision as U) and Brbar = (dR/dB_r)^T Rbar (FP64 [n_theta][n_phi]),
- * both overwritten.  Rbar_dev has the layout of R.  Brbar_dev may be NULL. */
+/* Vector-Jacobian product of the residual (the adjoint of every step of
+ * crn_residual: recovery, ghosts, limited reconstruction, Rusanov + GLM flux,
+ * accumulation, gravity): Ubar = (dR/dU)^T Rbar (same layout and precision as
+ * U) and Brbar = (dR/dB_r)^T Rbar (FP64 [n_theta][n_phi]), both overwritten.
+ * Rbar_dev has the layout of R.  Brbar_dev may be NULL.  Face states are
+ * recomputed, not stored.  Non-smooth points: max passes the derivative to
+ * its first argument on a tie, d|x|/dx = +1 at 0.  The first call on a grid
+ * allocates its scratch (36 values of the grid's type per face, about 108 per
+ * cell): make it before any stream capture.  Asynchronous, 4 launches. */
 int crn_residual_vjp(crn_grid* g, const void* U_dev, const void* Rbar_dev, void* Ubar_dev,
                      double* Brbar_dev, void* stream);
 

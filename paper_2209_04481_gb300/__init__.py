@@ -18,8 +18,8 @@ import ctypes
 import os
 import threading
 
-__all__ = ["Grid", "load_library", "CoronaError", "FP64", "FP32_BULK", "LIMITERS",
-           "KERNEL_TILED", "KERNEL_CELLWISE", "exported_symbols"]
+__all__ = ["Grid", "Residual", "residual", "load_library", "CoronaError", "FP64", "FP32_BULK",
+           "LIMITERS", "KERNEL_TILED", "KERNEL_CELLWISE", "exported_symbols"]
 
 FP64, FP32_BULK = 0, 1
 KERNEL_TILED, KERNEL_CELLWISE = 0, 1
@@ -195,12 +195,15 @@ class Grid:
                                  _stream_handle(stream)))
         return R
 
-    def residual_vjp(self, U, Rbar, Ubar=None, Brbar=None, stream=None):
+    def residual_vjp(self, U, Rbar, Ubar=None, Brbar=None, want_br=True, stream=None):
+        """(Ubar, Brbar) = ((dR/dU)^T Rbar, (dR/dB_r)^T Rbar) through crn_residual_vjp."""
         import torch
         self._state_check(U, "U")
         self._state_check(Rbar, "Rbar")
         if Ubar is None:
             Ubar = torch.empty_like(U)
+        if Brbar is None and want_br:
+            Brbar = torch.empty(self.shape[1:], dtype=torch.float64, device=U.device)
         _check(_lib.crn_residual_vjp(self._h, _ptr(U), _ptr(Rbar), _ptr(Ubar), _ptr(Brbar),
                                      _stream_handle(stream)))
         return Ubar, Brbar
@@ -238,3 +241,52 @@ class Grid:
             self.residual(Ud, Rd, norms, dtmin, stream=s)
             R_host.copy_(Rd, non_blocking=True)
         return R_host
+
+
+def _make_residual_function():
+    import torch
+
+    class Residual(torch.autograd.Function):
+        """R = dU/dt as a differentiable function of (U, B_r) on a Grid.
+
+        forward: crn_set_inner_boundary + crn_residual; backward: the
+        hand-written adjoint crn_residual_vjp (gradients for U and B_r).
+        """
+
+        @staticmethod
+        def forward(ctx, U, Br, grid):
+            grid.set_inner_boundary(Br)
+            R = grid.residual(U.contiguous())
+            ctx.save_for_backward(U, Br)
+            ctx.grid = grid
+            return R
+
+        @staticmethod
+        def backward(ctx, Rbar):
+            U, Br = ctx.saved_tensors
+            grid = ctx.grid
+            grid.set_inner_boundary(Br)
+            Ubar, Brbar = grid.residual_vjp(U.contiguous(), Rbar.contiguous(),
+                                            want_br=ctx.needs_input_grad[1])
+            return Ubar, Brbar, None
+
+    return Residual
+
+
+class _Lazy:
+    fn = None
+
+
+def residual(U, Br, grid):
+    """Differentiable residual (see Residual)."""
+    if _Lazy.fn is None:
+        _Lazy.fn = _make_residual_function()
+    return _Lazy.fn.apply(U, Br, grid)
+
+
+def __getattr__(name):
+    if name == "Residual":
+        if _Lazy.fn is None:
+            _Lazy.fn = _make_residual_function()
+        return _Lazy.fn
+    raise AttributeError(name)

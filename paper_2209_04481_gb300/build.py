@@ -23,7 +23,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
           "--expt-relaxed-constexpr"]
 # FP32-bulk translation unit: fast single-precision division and square root
-EXTRA = {"residual_fp32.cu": ["-prec-div=false", "-prec-sqrt=false"]}
+EXTRA = {"residual_fp32.cu": ["-prec-div=false", "-prec-sqrt=false"],
+         "vjp_fp32.cu": ["-prec-div=false", "-prec-sqrt=false"]}
 
 
 def nvcc() -> str:

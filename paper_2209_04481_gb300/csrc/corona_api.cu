@@ -205,6 +205,7 @@ void free_grid(crn_grid* g) {
   cudaFree(g->err_cell);
   cudaFree(g->rbuf);
   cudaFree(g->shadow);
+  cudaFree(g->vjp_buf);
   delete g;
 }
 
@@ -374,9 +375,33 @@ int crn_residual(crn_grid* g, const void* U_dev, void* R_dev, double* norms9_dev
 
 int crn_residual_vjp(crn_grid* g, const void* U_dev, const void* Rbar_dev, void* Ubar_dev,
                      double* Brbar_dev, void* stream) {
-  (void)U_dev; (void)Rbar_dev; (void)Ubar_dev; (void)Brbar_dev; (void)stream;
-  if (!g) return fail(CRN_E_ARG, "grid is NULL");
-  return fail(CRN_E_STATE, "crn_residual_vjp is not available in this build");
+  int rc = check_ready(g);
+  if (rc != CRN_OK) return rc;
+  if (!U_dev || !Rbar_dev || !Ubar_dev) return fail(CRN_E_ARG, "U_dev, Rbar_dev and Ubar_dev must not be NULL");
+  const size_t bytes = (size_t)9 * g->shape.ncell * elem_size(g);
+  const char* u = (const char*)U_dev;
+  const char* rb = (const char*)Rbar_dev;
+  const char* ub = (const char*)Ubar_dev;
+  if ((ub < u + bytes && u < ub + bytes) || (ub < rb + bytes && rb < ub + bytes))
+    return fail(CRN_E_ARG, "Ubar_dev overlaps U_dev or Rbar_dev");
+  if (!is_device_ptr(U_dev) || !is_device_ptr(Rbar_dev) || !is_device_ptr(Ubar_dev) ||
+      (Brbar_dev && !is_device_ptr(Brbar_dev)))
+    return fail(CRN_E_ARG, "VJP arguments must be device pointers");
+  if (!g->vjp_buf) {  // first VJP call of this grid: face-contribution scratch
+    cudaError_t e = cudaMalloc(&g->vjp_buf, crn::vjp_scratch_bytes(g));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(VJP scratch)");
+  }
+  int nl = 0;
+  cudaError_t e;
+  if (g->d.precision == CRN_FP64)
+    e = crn::launch_vjp_fp64(g, (const double*)U_dev, (const double*)Rbar_dev, (double*)Ubar_dev,
+                             Brbar_dev, (cudaStream_t)stream, &nl);
+  else
+    e = crn::launch_vjp_fp32(g, (const float*)U_dev, (const float*)Rbar_dev, (float*)Ubar_dev,
+                             Brbar_dev, (cudaStream_t)stream, &nl);
+  g->last_launches = nl;
+  if (e != cudaSuccess) return cuda_fail(e, "crn_residual_vjp launch");
+  return CRN_OK;
 }
 
 int crn_pseudo_time_step(crn_grid* g, double* U64_dev, int32_t nsteps, double cfl,

@@ -42,6 +42,7 @@ struct crn_grid {
   unsigned int* err_flags = nullptr;
   unsigned long long* err_cell = nullptr;
   void* rbuf = nullptr;            // residual scratch for pseudo-time stepping (9N of T)
+  void* vjp_buf = nullptr;         // VJP face contributions (allocated by the first VJP call)
   float* shadow = nullptr;         // FP32 shadow of the master state (FP32_BULK)
   int64_t last_bad_cell = -1;
   int32_t last_launches = 0;
@@ -58,6 +59,11 @@ cudaError_t launch_residual_fp32(crn_grid* g, const float* U, float* R, double* 
 cudaError_t launch_update(crn_grid* g, double* U64, double cfl, double* res_out,
                           cudaStream_t st, int* nlaunch);
 cudaError_t launch_shadow(crn_grid* g, const double* U64, cudaStream_t st, int* nlaunch);
+cudaError_t launch_vjp_fp64(crn_grid* g, const double* U, const double* Rb, double* Ub, double* Brb,
+                            cudaStream_t st, int* nlaunch);
+cudaError_t launch_vjp_fp32(crn_grid* g, const float* U, const float* Rb, float* Ub, double* Brb,
+                            cudaStream_t st, int* nlaunch);
+size_t vjp_scratch_bytes(const crn_grid* g);
 
 // shared-memory footprint of the tiled kernel for one precision
 size_t tiled_smem_fp64();
