@@ -37,17 +37,26 @@ R_IN, R_OUT = 1.0, 21.5
 PARKER_RC = 5.0               # sonic-point radius of the background wind
 
 
-def radial_faces(n_r, r_in=R_IN, r_out=R_OUT):
-    """Geometric radial stretch r_k = r_in (r_out/r_in)^(k/N_r), k = 0..N_r."""
-    k = np.arange(n_r + 1, dtype=np.float64)
-    rf = r_in * (r_out / r_in) ** (k / n_r)
-    rf[0], rf[-1] = r_in, r_out
+def radial_faces(n_r, r_in=R_IN, r_out=R_OUT, r_last=None):
+    """Geometric radial stretch r_k = r_in (r_top/r_in)^(k/M), k = 0..M.
+
+    Without ``r_last``: M = N_r, r_top = r_out.  With it (the mesh of Sect. 4.3
+    with a thin outermost cell): M = N_r - 1 cells up to r_top = r_last, then
+    one cell [r_last, r_out].
+    """
+    M = n_r - 1 if r_last else n_r
+    r_top = r_last if r_last else r_out
+    k = np.arange(M + 1, dtype=np.float64)
+    rf = r_in * (r_top / r_in) ** (k / M)
+    rf[0], rf[-1] = r_in, r_top
+    if r_last:
+        rf = np.append(rf, r_out)
     return rf
 
 
-def cell_centres(n_r, n_theta, n_phi, r_in=R_IN, r_out=R_OUT):
+def cell_centres(n_r, n_theta, n_phi, r_in=R_IN, r_out=R_OUT, r_last=None):
     """Coordinate midpoints (r_c, theta_c, phi_c) as 1D arrays."""
-    rf = radial_faces(n_r, r_in, r_out)
+    rf = radial_faces(n_r, r_in, r_out, r_last)
     rc = 0.5 * (rf[:-1] + rf[1:])
     tf = math.pi * np.arange(n_theta + 1) / n_theta
     pf = 2.0 * math.pi * np.arange(n_phi + 1) / n_phi
@@ -92,14 +101,18 @@ def dipole_field(r, theta, phi):
 
 
 def background(n_r, n_theta, n_phi, gamma=GAMMA, g0=G0_SOLAR, r_c=PARKER_RC,
-               r_in=R_IN, r_out=R_OUT):
+               r_in=R_IN, r_out=R_OUT, r_last=None, efree=False):
     """Parker wind + aligned dipole on cell centres.
 
     Returns (U, info): U is the conservative SoA state of shape
     (9, n_r, n_theta, n_phi) float64; info holds rho_b, p_b (the inner boundary
     density and pressure: the wind at r = r_in), c_s^2 and the primitives.
+
+    ``efree``: the electric-field-free start of Sect. 3.1 -- the Parker speed is
+    kept but the velocity is turned along the field, V = v sgn(B_r) B/|B|
+    (sgn 0 = +1), so that V x B = 0 in every cell.  Otherwise V is radial.
     """
-    rc, tc, pc = cell_centres(n_r, n_theta, n_phi, r_in, r_out)
+    rc, tc, pc = cell_centres(n_r, n_theta, n_phi, r_in, r_out, r_last)
     R, T, P = np.meshgrid(rc, tc, pc, indexing="ij")
     cs2 = parker_sound_speed2(g0, r_c)
     cs = math.sqrt(cs2)
@@ -109,8 +122,14 @@ def background(n_r, n_theta, n_phi, gamma=GAMMA, g0=G0_SOLAR, r_c=PARKER_RC,
     rho = (m_in / mach) * (r_in / R) ** 2        # rho v r^2 = const, rho(r_in) = 1
     p = rho * cs2
     st, ct, sp, cp = np.sin(T), np.cos(T), np.sin(P), np.cos(P)
-    vx, vy, vz = v * st * cp, v * st * sp, v * ct
     bx, by, bz = dipole_field(R, T, P)
+    if efree:
+        bmag = np.sqrt(bx * bx + by * by + bz * bz)
+        br = bx * st * cp + by * st * sp + bz * ct
+        f = v * np.where(br < 0.0, -1.0, 1.0) / bmag
+        vx, vy, vz = f * bx, f * by, f * bz
+    else:
+        vx, vy, vz = v * st * cp, v * st * sp, v * ct
     W = np.stack([rho, vx, vy, vz, bx, by, bz, p, np.zeros_like(rho)])
     U = prim_to_cons(W, gamma)
     info = {"rho_b": 1.0, "p_b": cs2, "cs2": cs2, "W": W}
@@ -161,6 +180,59 @@ def real_sh(lmax, theta, phi):
                 Y = math.sqrt(2.0) * P[l][-m] * np.sin(-m * phi)
             out.append((l, m, Y))
     return out
+
+
+def potential_field(n_theta, n_phi, lmax=15, seed=2209, target_max=5.0, dipole_only=False,
+                    dtheta=1e-6):
+    """(B_r, B_theta) at r = 1 of the source-free exterior potential field whose
+    radial component is ``magnetogram(...)``: B = -grad Phi with
+    Phi = sum_lm a_lm r^-(l+1) Y_lm / (l + 1), so B_theta(r=1) =
+    -sum_lm a_lm / (l + 1) dY_lm/dtheta (the dipole part cos(theta) gives
+    sin(theta)/2).  It stands in for the PFSS B_theta that the paper's large-E
+    boundary prescribes (Sect. 3.2).  Returns shape (2, n_theta, n_phi)."""
+    br = magnetogram(n_theta, n_phi, lmax=lmax, seed=seed, target_max=target_max,
+                     dipole_only=dipole_only)
+    _, tc, pc = cell_centres(2, n_theta, n_phi)
+    T, P = np.meshgrid(tc, pc, indexing="ij")
+    bt = 0.5 * np.sin(T)
+    if not dipole_only:
+        scale = _magnetogram_scale(n_theta, n_phi, lmax, seed, target_max)
+        rng = np.random.default_rng(seed)
+        hi = real_sh(lmax, T + dtheta, P)
+        lo = real_sh(lmax, T - dtheta, P)
+        for (l, m, Yp), (_, _, Ym) in zip(hi, lo):
+            if l == 0:
+                continue
+            a = rng.standard_normal() / l
+            bt -= scale * a / (l + 1) * (Yp - Ym) / (2.0 * dtheta)
+    return np.stack([br, bt])
+
+
+def _magnetogram_scale(n_theta, n_phi, lmax, seed, target_max):
+    """The factor s of magnetogram(): max |cos(theta) + s f| = target_max."""
+    _, tc, pc = cell_centres(2, n_theta, n_phi)
+    T, P = np.meshgrid(tc, pc, indexing="ij")
+    dip = np.cos(T)
+    rng = np.random.default_rng(seed)
+    f = np.zeros_like(T)
+    for (l, m, Y) in real_sh(lmax, T, P):
+        if l == 0:
+            continue
+        f += (rng.standard_normal() / l) * Y
+
+    def peak(s):
+        return float(np.max(np.abs(dip + s * f)))
+    hi = 1.0
+    while peak(hi) < target_max:
+        hi *= 2.0
+    lo = 0.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if peak(mid) < target_max:
+            lo = mid
+        else:
+            hi = mid
+    return hi
 
 
 def magnetogram(n_theta, n_phi, lmax=15, seed=2209, target_max=5.0, dipole_only=False):

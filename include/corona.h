@@ -57,12 +57,20 @@ typedef enum {
 typedef enum { CRN_FP64 = 0, CRN_FP32_BULK = 1 } crn_precision;
 typedef enum { CRN_LIM_NONE = 0, CRN_LIM_MINMOD = 1, CRN_LIM_VANALBADA = 2 } crn_limiter;
 typedef enum { CRN_KERNEL_TILED = 0, CRN_KERNEL_CELLWISE = 1 } crn_kernel;
+/* Inner-boundary formulation (Sect. 3.2): LOW_E: B_r prescribed, B_theta and
+ * B_phi Neumann, V_b parallel to B_b (E_b = 0).  LARGE_E: the Wind-Predict
+ * form, B_r and B_theta prescribed (from a potential field), B_phi Neumann,
+ * V_b = V_par (B_r rhat + B_theta thetahat), V_par = V_r* B_r / B_pol^2. */
+typedef enum { CRN_INNER_LOW_E = 0, CRN_INNER_LARGE_E = 1 } crn_inner_bc;
 
 /* Grid and physics description.  crn_grid_desc_default fills the solar-wind
  * defaults: r in [1, 21.5], gamma = 1.05, c_h = 1, g0 = 0.8271 (G M_sun /
  * (R_sun V_ref^2) with V_ref = B_ref / sqrt(mu0 rho_ref) of Sect. 2.1), van
- * Albada limiter with eps = 1e-12, outer exponents a = b = 2 (Table 2 case 3),
- * rho_b = 1, p_b = 0.0827, FP32_BULK, tiled kernel. */
+ * Albada limiter with eps = 1e-12, outer laws of Table 2 case 3 (a = b = 2,
+ * B_phi, V zero-gradient, psi_b = 0), rho_b = 1, p_b = 0.0827, low-E inner
+ * boundary, V_r* = 1935.07 m/s / V_ref (Sect. 3.2) for the large-E form,
+ * FP32_BULK, tiled kernel.  The outer laws cover all cases of Table 2 and the
+ * rho ~ r^-2.5 law of Sect. 4.2 (outer_rho_exp = 2.5). */
 typedef struct {
   int32_t n_r, n_theta, n_phi;  /* cells; n_phi even and a multiple of 8         */
   int32_t precision;            /* crn_precision                                 */
@@ -76,6 +84,17 @@ typedef struct {
   double outer_rho_exp;         /* outer ghost rho, p scaled by (r_I/r_G)^a      */
   double outer_br_exp;          /* outer ghost B_r scaled by (r_I/r_G)^b         */
   double rho_b, p_b;            /* inner boundary density and pressure, > 0      */
+  int32_t inner_bc;             /* crn_inner_bc                                  */
+  int32_t outer_vr_mass;        /* outer ghost V_r: 0 zero-gradient, 1 V_r r^2 rho = const */
+  int32_t outer_psi_extrap;     /* outer ghost psi: 0 psi_b = 0, 1 zero-gradient */
+  int32_t reserved_;            /* must be 0                                     */
+  double vr_star;               /* large-E: prescribed radial outflow V_r*       */
+  double outer_bphi_exp;        /* outer ghost B_phi scaled by (r_I/r_G)^c       */
+  double outer_vphi_exp;        /* outer ghost V_phi scaled by (r_I/r_G)^e       */
+  double r_last;                /* 0: geometric radial faces r_k = r_in (r_out/r_in)^(k/n_r);
+                                   in (r_in, r_out): n_r - 1 geometric cells up to r_last
+                                   and one thin last cell [r_last, r_out], the mesh with a
+                                   small outer ghost of Sect. 4.3 (not for crn_residual_static) */
 } crn_grid_desc;
 
 typedef struct crn_grid crn_grid;
@@ -101,7 +120,8 @@ int crn_grid_destroy(crn_grid* g);
 
 /* Prescribe the inner-boundary radial field B_r [Sect. 1 and 3.2: B_r from the
  * magnetogram at the inner boundary].  Br_dev: FP64 device array
- * [n_theta][n_phi], B_r at the inner face centres (theta_c, phi_c); copied
+ * [n_theta][n_phi], B_r at the inner face centres (theta_c, phi_c); for
+ * CRN_INNER_LARGE_E grids [2][n_theta][n_phi]: B_r, then B_theta.  Copied
  * into grid-owned storage asynchronously on the stream (the caller may reuse
  * its buffer once the stream has passed this point).  Must precede the first
  * residual / pseudo-time call (CRN_E_STATE otherwise). */
@@ -121,7 +141,8 @@ int crn_residual(crn_grid* g, const void* U_dev, void* R_dev, double* norms9_dev
  * crn_residual: recovery, ghosts, limited reconstruction, Rusanov + GLM flux,
  * accumulation, gravity): Ubar = (dR/dU)^T Rbar (same layout and precision as
  * U) and Brbar = (dR/dB_r)^T Rbar (FP64 [n_theta][n_phi]), both overwritten.
- * Rbar_dev has the layout of R.  Brbar_dev may be NULL.  Face states are
+ * Rbar_dev has the layout of R.  Brbar_dev may be NULL; for CRN_INNER_LARGE_E
+ * grids it is [2][n_theta][n_phi] (cotangents of B_r and B_theta).  Face states are
  * recomputed, not stored.  Non-smooth points: max passes the derivative to
  * its first argument on a tie, d|x|/dx = +1 at 0.  The first call on a grid
  * allocates its scratch (36 values of the grid's type per face, about 108 per
@@ -150,6 +171,7 @@ int crn_pseudo_time_step(crn_grid* g, double* U64_dev, int32_t nsteps, double cf
  * (d->kernel is ignored; the tiled kernel is used).  Br_dev: FP64 device
  * array [n_theta][n_phi] read during the call; U_dev, R_dev, norms9_dev,
  * dtmin_dev as for crn_residual (norms9_dev, dtmin_dev may be NULL).
+ * For CRN_INNER_LARGE_E descriptors Br_dev holds [2][n_theta][n_phi].
  * Scratch (geometry, reduction partials, arrival counter, error word) is one
  * fixed device array of about 3.6 MB inside the library, held by every GPU
  * that loads the library until process exit.  Limits: n_r <= 1024,
@@ -166,6 +188,20 @@ int crn_pseudo_time_step(crn_grid* g, double* U64_dev, int32_t nsteps, double cf
  * cudaFree or other allocating routine.  Asynchronous on `stream`. */
 int crn_residual_static(const crn_grid_desc* d, const double* Br_dev, const void* U_dev,
                         void* R_dev, double* norms9_dev, double* dtmin_dev, void* stream);
+
+/* Boundary electric field diagnostic [Sect. 2.2: E = -V x B; Sect. 3.2
+ * compares the inner-boundary E of the low-E and large-E formulations]:
+ * E_dev[3][n_theta][n_phi] (FP64, Cartesian components) receives
+ * E = -V_b x B_b of the face-mean state (ghost + interior) / 2 at every inner
+ * face, computed in FP64 from U_dev (the grid's precision).  Asynchronous. */
+int crn_boundary_efield(crn_grid* g, const void* U_dev, double* E_dev, void* stream);
+
+/* Volume electric field [Sect. 2.2: E = -V x B; Sect. 3.1 traces spurious E to
+ * the initial state and to the inner boundary]: E_dev[3][n_r][n_theta][n_phi]
+ * (FP64, Cartesian components) receives E = -(m x B) / rho of every cell,
+ * computed in FP64 from U_dev (the grid's precision).  Needs no inner
+ * boundary values.  Asynchronous on `stream`; one launch. */
+int crn_efield(crn_grid* g, const void* U_dev, double* E_dev, void* stream);
 
 /* Synchronise the stream, then read and clear the grid's device error word.
  * Returns CRN_E_NONPHYSICAL if a kernel saw a non-physical state since the

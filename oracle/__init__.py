@@ -62,6 +62,10 @@ class _Desc(ctypes.Structure):
         ("gamma", ctypes.c_double), ("c_h", ctypes.c_double), ("g0", ctypes.c_double),
         ("outer_rho_exp", ctypes.c_double), ("outer_br_exp", ctypes.c_double),
         ("rho_b", ctypes.c_double), ("p_b", ctypes.c_double),
+        ("inner_bc", ctypes.c_int32), ("outer_vr_mass", ctypes.c_int32),
+        ("outer_psi_extrap", ctypes.c_int32), ("pad_", ctypes.c_int32),
+        ("vr_star", ctypes.c_double), ("outer_bphi_exp", ctypes.c_double),
+        ("outer_vphi_exp", ctypes.c_double), ("r_last", ctypes.c_double),
     ]
 
 
@@ -78,6 +82,10 @@ def _load():
             lib.orc_cons_to_prim.argtypes = [D, P, P]
             lib.orc_geometry.argtypes = [D, P, P, P, P]
             lib.orc_ghosts.argtypes = [D, P, P, P, P]
+            lib.orc_boundary_efield.argtypes = [D, P, P, P]
+            lib.orc_boundary_efield.restype = ctypes.c_int
+            lib.orc_efield.argtypes = [D, P, P]
+            lib.orc_efield.restype = ctypes.c_int
             lib.orc_pseudo_time_step.argtypes = [D, P, P, ctypes.c_int, ctypes.c_double, P, P]
             for f in (lib.orc_residual, lib.orc_residual_jvp, lib.orc_flux, lib.orc_cons_to_prim,
                       lib.orc_geometry, lib.orc_ghosts, lib.orc_pseudo_time_step):
@@ -108,6 +116,13 @@ class Grid:
     outer_br_exp: float = 2.0
     rho_b: float = 1.0
     p_b: float = 0.0
+    inner_bc: str = "low_e"          # "low_e" | "large_e"
+    vr_star: float = 0.0
+    outer_bphi_exp: float = 0.0
+    outer_vphi_exp: float = 0.0
+    outer_vr_mass: bool = False
+    outer_psi_extrap: bool = False
+    r_last: float = 0.0              # > 0: thin last cell [r_last, r_out] (Sect. 4.3)
     geom: int = GEOM_SPHERE
     lengths: tuple = (1.0, 1.0, 1.0)
     bcs: tuple = (BC_PERIODIC, BC_PERIODIC, BC_PERIODIC)
@@ -133,7 +148,19 @@ class Grid:
         d.gamma, d.c_h, d.g0 = self.gamma, self.c_h, self.g0
         d.outer_rho_exp, d.outer_br_exp = self.outer_rho_exp, self.outer_br_exp
         d.rho_b, d.p_b = self.rho_b, self.p_b
+        d.inner_bc = {"low_e": 0, "large_e": 1}[self.inner_bc]
+        d.outer_vr_mass = int(bool(self.outer_vr_mass))
+        d.outer_psi_extrap = int(bool(self.outer_psi_extrap))
+        d.vr_star = self.vr_star
+        d.outer_bphi_exp, d.outer_vphi_exp = self.outer_bphi_exp, self.outer_vphi_exp
+        d.r_last = self.r_last
         return d
+
+    @property
+    def boundary_shape(self):
+        """Shape of the inner-boundary input: B_r, or (B_r, B_theta) for large-E."""
+        nb = 2 if self.inner_bc == "large_e" else 1
+        return (self.n_theta, self.n_phi) if nb == 1 else (2, self.n_theta, self.n_phi)
 
 
 def box(nx, ny, nz, lengths=(1.0, 1.0, 1.0), bcs=(BC_PERIODIC,) * 3, **kw) -> Grid:
@@ -165,7 +192,7 @@ def residual(grid: Grid, U, Br=None, want_scale=False, want_bflux=False):
     lib = _load()
     U = _f64(U, (9,) + grid.shape)
     if grid.geom == GEOM_SPHERE:
-        Br = _f64(Br, (grid.n_theta, grid.n_phi))
+        Br = _f64(Br, grid.boundary_shape)
     R = np.empty_like(U)
     norms = np.empty(9)
     dtmin = np.empty(1)
@@ -190,8 +217,8 @@ def residual_jvp(grid: Grid, U, Br, dU, dBr):
     U = _f64(U, (9,) + grid.shape)
     dU = _f64(dU, (9,) + grid.shape)
     if grid.geom == GEOM_SPHERE:
-        Br = _f64(Br, (grid.n_theta, grid.n_phi))
-        dBr = _f64(dBr, (grid.n_theta, grid.n_phi))
+        Br = _f64(Br, grid.boundary_shape)
+        dBr = _f64(dBr, grid.boundary_shape)
     R = np.empty_like(U)
     dR = np.empty_like(U)
     d = grid.desc()
@@ -240,7 +267,7 @@ def ghosts(grid: Grid, U, Br):
     """Primitive ghost planes (inner, outer), each of shape (9, n_theta, n_phi)."""
     lib = _load()
     U = _f64(U, (9,) + grid.shape)
-    Br = _f64(Br, (grid.n_theta, grid.n_phi))
+    Br = _f64(Br, grid.boundary_shape)
     Win = np.empty((9, grid.n_theta, grid.n_phi))
     Wout = np.empty_like(Win)
     d = grid.desc()
@@ -254,7 +281,7 @@ def pseudo_time_step(grid: Grid, U, Br, nsteps: int, cfl: float):
     lib = _load()
     U = _f64(U, (9,) + grid.shape).copy()
     if grid.geom == GEOM_SPHERE:
-        Br = _f64(Br, (grid.n_theta, grid.n_phi))
+        Br = _f64(Br, grid.boundary_shape)
     res = np.empty((max(nsteps, 1), 9))
     dts = np.empty(max(nsteps, 1))
     d = grid.desc()
@@ -262,3 +289,25 @@ def pseudo_time_step(grid: Grid, U, Br, nsteps: int, cfl: float):
                                 _ptr(res), _ptr(dts)):
         raise ValueError("bad description")
     return U, res[:nsteps], dts[:nsteps]
+
+
+def efield(grid: Grid, U):
+    """Cell-centred E = -V x B of every cell, shape (3, n_r, n_theta, n_phi)."""
+    lib = _load()
+    U = _f64(U, (9,) + grid.shape)
+    E = np.empty((3,) + grid.shape)
+    if lib.orc_efield(ctypes.byref(grid.desc()), _ptr(U), _ptr(E)):
+        raise ValueError("bad description")
+    return E
+
+
+def boundary_efield(grid: Grid, U, Br):
+    """E = -V_b x B_b of the face-mean state at the inner faces, shape (3, n_theta, n_phi)."""
+    lib = _load()
+    U = _f64(U, (9,) + grid.shape)
+    Br = _f64(Br, grid.boundary_shape)
+    E = np.empty((3, grid.n_theta, grid.n_phi))
+    d = grid.desc()
+    if lib.orc_boundary_efield(ctypes.byref(d), _ptr(U), _ptr(Br), _ptr(E)):
+        raise ValueError("bad description")
+    return E

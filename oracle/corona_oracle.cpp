@@ -105,6 +105,14 @@ typedef struct {
   double outer_rho_exp;    // outer ghost: rho, p scaled by (r_I/r_G)^a
   double outer_br_exp;     // outer ghost: B_r scaled by (r_I/r_G)^b
   double rho_b, p_b;       // inner boundary density and pressure
+  int32_t inner_bc;        // 0 low-E (Sect. 3.2), 1 large-E / Wind-Predict (Sect. 3.2)
+  int32_t outer_vr_mass;   // outer ghost V_r: 0 zero-gradient, 1 V_r r^2 rho = const
+  int32_t outer_psi_extrap;// outer ghost psi: 0 psi_b = 0, 1 zero-gradient (G = I)
+  int32_t pad_;
+  double vr_star;          // large-E: prescribed radial outflow V_r*
+  double outer_bphi_exp;   // outer ghost: B_phi scaled by (r_I/r_G)^c
+  double outer_vphi_exp;   // outer ghost: V_phi scaled by (r_I/r_G)^e
+  double r_last;           // 0: geometric faces; else the last cell is [r_last, r_out] (Sect. 4.3)
 } orc_desc;
 }
 
@@ -215,10 +223,16 @@ struct Mesh {
     ncell = (long)n[0] * n[1] * n[2];
     if (d.geom == GEOM_SPHERE) {
       rf.resize(n[0] + 1);
-      // geometric radial stretch: r_k = r_in (r_out/r_in)^(k/N_r)
-      for (int k = 0; k <= n[0]; ++k)
-        rf[k] = d.r_in * std::pow(d.r_out / d.r_in, double(k) / n[0]);
+      // geometric radial stretch r_k = r_in (r_top/r_in)^(k/M) over M cells;
+      // with r_last set (the boundary-condition-independent mesh of Sect. 4.3)
+      // M = N_r - 1 cells reach r_top = r_last and one thin cell closes at r_out
+      const bool thin = d.r_last > 0.0;
+      const int M = thin ? n[0] - 1 : n[0];
+      const double r_top = thin ? d.r_last : d.r_out;
+      for (int k = 0; k <= M; ++k)
+        rf[k] = d.r_in * std::pow(r_top / d.r_in, double(k) / M);
       rf[0] = d.r_in;
+      rf[M] = r_top;
       rf[n[0]] = d.r_out;
     }
   }
@@ -239,6 +253,18 @@ struct Mesh {
     e[0] = std::sin(t) * std::cos(p);
     e[1] = std::sin(t) * std::sin(p);
     e[2] = std::cos(t);
+  }
+  void thetahat(int j, int i, double e[3]) const {
+    double t = tc(j), p = pc(i);
+    e[0] = std::cos(t) * std::cos(p);
+    e[1] = std::cos(t) * std::sin(p);
+    e[2] = -std::sin(t);
+  }
+  void phihat(int i, double e[3]) const {
+    double p = pc(i);
+    e[0] = -std::sin(p);
+    e[1] = std::cos(p);
+    e[2] = 0.0;
   }
 
   double h(int ax) const {  // box spacing
@@ -298,13 +324,39 @@ struct Mesh {
 // ---------------------------------------------------------------------------
 // ghost states
 // ---------------------------------------------------------------------------
+// Inner "large-E" ghost (the Wind-Predict formulation of Sect. 3.2): B_r and
+// B_theta prescribed (from a potential field), B_phi Neumann; the poloidal
+// velocity V_par (B_r rhat + B_theta thetahat) with V_par = V_r* B_r / B_pol^2,
+// B_pol^2 = B_r^2 + B_theta^2, so V_r,b = V_par B_r, V_theta,b = V_par B_theta,
+// V_phi,b = 0.  Ghost = 2 * boundary - interior; rho, p Dirichlet; psi_b = 0.
+template <class T>
+void large_e_ghost(const Mesh& m, int j, int i, const T wi[9], T br, T bt, T wg[9]) {
+  double er[3], et[3], ep[3];
+  m.rhat(j, i, er);
+  m.thetahat(j, i, et);
+  m.phihat(i, ep);
+  T bip = wi[W_BX] * ep[0] + wi[W_BY] * ep[1] + wi[W_BZ] * ep[2];
+  T bpol2 = br * br + bt * bt;
+  T vpar = m.d.vr_star * br / vmax(bpol2, T(1e-300));
+  wg[W_RHO] = T(m.d.rho_b);
+  wg[W_P] = T(m.d.p_b);
+  for (int c = 0; c < 3; ++c) {
+    T bb = br * er[c] + bt * et[c] + bip * ep[c];
+    T vb = vpar * (br * er[c] + bt * et[c]);
+    wg[W_VX + c] = 2.0 * vb - wi[W_VX + c];
+    wg[W_BX + c] = 2.0 * bb - wi[W_BX + c];
+  }
+  wg[W_PSI] = -wi[W_PSI];
+}
+
 // Inner "low-E" ghost at r = r_in for column (j, i) from the interior
 // primitive state wi and the prescribed B_r [Sect. 3.2: V_b x B_b = 0 fixes the
 // direction of V_b; B_r from the magnetogram; B_theta, B_phi Neumann;
 // Sect. 3.3: psi_b = 0].  Ghost = 2 * boundary - interior (face mean equals the
 // boundary value) for B and V; rho, p Dirichlet at the ghost centre.
 template <class T>
-void inner_ghost(const Mesh& m, int j, int i, const T wi[9], T br, T wg[9]) {
+void inner_ghost(const Mesh& m, int j, int i, const T wi[9], T br, T bt, T wg[9]) {
+  if (m.d.inner_bc == 1) { large_e_ghost(m, j, i, wi, br, bt, wg); return; }
   double e[3];
   m.rhat(j, i, e);
   T bi[3] = {wi[W_BX], wi[W_BY], wi[W_BZ]};
@@ -325,25 +377,37 @@ void inner_ghost(const Mesh& m, int j, int i, const T wi[9], T br, T wg[9]) {
   wg[W_PSI] = -wi[W_PSI];
 }
 
-// Outer ghost at r = r_out [Sect. 4.1, Table 2 case 3 by default]:
-// rho_G = rho_I (r_I/r_G)^a, p likewise, B_r,G = B_r,I (r_I/r_G)^b with the
-// tangential B, and V, zero-gradient; psi_b = 0 (Dirichlet on the boundary).
+// Outer ghost at r = r_out [Sect. 4.1, Table 2; case 3 by default]: with
+// s = r_I / r_G (ghost centre mirrored about the boundary),
+//   rho_G = rho_I s^a, p_G = p_I s^a                (rho r^a = const),
+//   B_r,G = B_r,I s^b, B_phi,G = B_phi,I s^c, B_theta zero-gradient,
+//   V_r,G = V_r,I s^(2-a) if V_r r^2 rho = const, else zero-gradient,
+//   V_phi,G = V_phi,I s^e, V_theta zero-gradient,
+//   psi: psi_b = 0 (G = -I) or zero-gradient (G = I).
 template <class T>
 void outer_ghost(const Mesh& m, int j, int i, const T wi[9], T wg[9]) {
-  double e[3];
-  m.rhat(j, i, e);
+  double er[3], ep[3];
+  m.rhat(j, i, er);
+  m.phihat(i, ep);
   double rI = m.rc(m.n[0] - 1);
   double rG = 2.0 * m.d.r_out - rI;
-  double fa = std::pow(rI / rG, m.d.outer_rho_exp);
-  double fb = std::pow(rI / rG, m.d.outer_br_exp);
-  T bir = wi[W_BX] * e[0] + wi[W_BY] * e[1] + wi[W_BZ] * e[2];
+  double sr = rI / rG;
+  double fa = std::pow(sr, m.d.outer_rho_exp);
+  double fb = std::pow(sr, m.d.outer_br_exp);
+  double fbp = std::pow(sr, m.d.outer_bphi_exp);
+  double fvr = m.d.outer_vr_mass ? std::pow(sr, 2.0 - m.d.outer_rho_exp) : 1.0;
+  double fvp = std::pow(sr, m.d.outer_vphi_exp);
+  T bir = wi[W_BX] * er[0] + wi[W_BY] * er[1] + wi[W_BZ] * er[2];
+  T bip = wi[W_BX] * ep[0] + wi[W_BY] * ep[1] + wi[W_BZ] * ep[2];
+  T vir = wi[W_VX] * er[0] + wi[W_VY] * er[1] + wi[W_VZ] * er[2];
+  T vip = wi[W_VX] * ep[0] + wi[W_VY] * ep[1] + wi[W_VZ] * ep[2];
   wg[W_RHO] = wi[W_RHO] * fa;
   wg[W_P] = wi[W_P] * fa;
   for (int c = 0; c < 3; ++c) {
-    wg[W_VX + c] = wi[W_VX + c];
-    wg[W_BX + c] = wi[W_BX + c] + (bir * fb - bir) * e[c];
+    wg[W_VX + c] = wi[W_VX + c] + (vir * fvr - vir) * er[c] + (vip * fvp - vip) * ep[c];
+    wg[W_BX + c] = wi[W_BX + c] + (bir * fb - bir) * er[c] + (bip * fbp - bip) * ep[c];
   }
-  wg[W_PSI] = -wi[W_PSI];
+  wg[W_PSI] = m.d.outer_psi_extrap ? wi[W_PSI] : -wi[W_PSI];
 }
 
 // ---------------------------------------------------------------------------
@@ -371,7 +435,8 @@ struct State {
       for (int j = 0; j < nt; ++j)
         for (int i = 0; i < np; ++i) {
           long col = (long)j * np + i;
-          inner_ghost(m, j, i, &W[9 * m.idx(0, j, i)], Br[col], &Gin[9 * col]);
+          T bt = m.d.inner_bc == 1 ? Br[(long)nt * np + col] : T(0.0);
+          inner_ghost(m, j, i, &W[9 * m.idx(0, j, i)], Br[col], bt, &Gin[9 * col]);
           outer_ghost(m, j, i, &W[9 * m.idx(nr - 1, j, i)], &Gout[9 * col]);
         }
     }
@@ -551,6 +616,7 @@ bool desc_ok(const orc_desc* d) {
     if (d->n2 % 2 != 0) return false;  // across-pole ghosts need an even N_phi
     if (!(d->r_in > 0.0 && d->r_out > d->r_in)) return false;
     if (d->n0 < 2) return false;
+    if (d->r_last != 0.0 && !(d->r_last > d->r_in && d->r_last < d->r_out)) return false;
   } else if (d->geom != GEOM_BOX) {
     return false;
   }
@@ -609,7 +675,7 @@ int orc_residual_jvp(const orc_desc* d, const double* U, const double* Br,
   for (long q = 0; q < 9 * N; ++q) Ud[q] = Dual(U[q], dU[q]);
   std::vector<Dual> Bd;
   if (d->geom == GEOM_SPHERE) {
-    long nc = (long)d->n1 * d->n2;
+    long nc = (long)d->n1 * d->n2 * (d->inner_bc == 1 ? 2 : 1);
     Bd.resize(nc);
     for (long q = 0; q < nc; ++q) Bd[q] = Dual(Br[q], dBr[q]);
   }
@@ -664,6 +730,50 @@ int orc_geometry(const orc_desc* d, double* vol, double* S0, double* S1, double*
     for (int a = 0; a < n0; ++a)
       for (int b = 0; b < n1; ++b)
         for (int f = 0; f <= n2; ++f) m.face_vector(2, f, a, b, &S2[3 * (((long)a * n1 + b) * (n2 + 1) + f)]);
+  return 0;
+}
+
+// Electric field E = -V_b x B_b of the face-mean state at every inner face,
+// W_b = (W_ghost + W_interior) / 2 [Sect. 2.2: E = -V x B; Sect. 3.2 compares
+// the boundary E of the two inner formulations].  E[3][n1][n2].
+int orc_boundary_efield(const orc_desc* d, const double* U, const double* Br, double* E) {
+  if (!desc_ok(d) || d->geom != GEOM_SPHERE || !U || !Br || !E) return 1;
+  Mesh m(*d);
+  State<double> st(m, U, Br);
+  long nc = (long)d->n1 * d->n2;
+  for (int j = 0; j < d->n1; ++j)
+    for (int i = 0; i < d->n2; ++i) {
+      long col = (long)j * d->n2 + i;
+      const double* wg = &st.Gin[9 * col];
+      const double* wi = &st.W[9 * m.idx(0, j, i)];
+      double v[3], b[3];
+      for (int c = 0; c < 3; ++c) {
+        v[c] = 0.5 * (wg[W_VX + c] + wi[W_VX + c]);
+        b[c] = 0.5 * (wg[W_BX + c] + wi[W_BX + c]);
+      }
+      E[0 * nc + col] = -(v[1] * b[2] - v[2] * b[1]);
+      E[1 * nc + col] = -(v[2] * b[0] - v[0] * b[2]);
+      E[2 * nc + col] = -(v[0] * b[1] - v[1] * b[0]);
+    }
+  return 0;
+}
+
+// cell-centred E = -V x B of every interior cell (the field whose spurious
+// part Sect. 3.1 traces to the initial state and the inner boundary):
+// E [3][n0][n1][n2] for the Cartesian components.
+int orc_efield(const orc_desc* d, const double* U, double* E) {
+  if (!desc_ok(d) || !U || !E) return 1;
+  Mesh m(*d);
+  for (long c = 0; c < m.ncell; ++c) {
+    double u[9], w[9];
+    for (int v = 0; v < 9; ++v) u[v] = U[v * m.ncell + c];
+    cons_to_prim(u, d->gamma, w);
+    const double* V = &w[W_VX];
+    const double* B = &w[W_BX];
+    E[0 * m.ncell + c] = -(V[1] * B[2] - V[2] * B[1]);
+    E[1 * m.ncell + c] = -(V[2] * B[0] - V[0] * B[2]);
+    E[2 * m.ncell + c] = -(V[0] * B[1] - V[1] * B[0]);
+  }
   return 0;
 }
 

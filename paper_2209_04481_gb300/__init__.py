@@ -47,6 +47,10 @@ class GridDesc(ctypes.Structure):
         ("lim_eps", ctypes.c_double),
         ("outer_rho_exp", ctypes.c_double), ("outer_br_exp", ctypes.c_double),
         ("rho_b", ctypes.c_double), ("p_b", ctypes.c_double),
+        ("inner_bc", ctypes.c_int32), ("outer_vr_mass", ctypes.c_int32),
+        ("outer_psi_extrap", ctypes.c_int32), ("reserved_", ctypes.c_int32),
+        ("vr_star", ctypes.c_double), ("outer_bphi_exp", ctypes.c_double),
+        ("outer_vphi_exp", ctypes.c_double), ("r_last", ctypes.c_double),
     ]
 
 
@@ -81,6 +85,8 @@ def load_library(build_if_needed: bool = True):
             "crn_last_bad_cell": (ctypes.c_int64, [vp]),
             "crn_last_error": (ctypes.c_char_p, []),
             "crn_last_launch_count": (i32, [vp]),
+            "crn_boundary_efield": (ctypes.c_int, [vp, vp, vp, vp]),
+            "crn_efield": (ctypes.c_int, [vp, vp, vp, vp]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(lib, name)
@@ -132,6 +138,8 @@ class Grid:
         d.precision = {"fp64": FP64, "fp32": FP32_BULK, "fp32_bulk": FP32_BULK}[precision]
         d.limiter = LIMITERS[limiter]
         d.kernel = {"tiled": KERNEL_TILED, "cellwise": KERNEL_CELLWISE}[kernel]
+        if "inner_bc" in kw and isinstance(kw["inner_bc"], str):
+            kw["inner_bc"] = {"low_e": 0, "large_e": 1}[kw["inner_bc"]]
         for k, v in kw.items():
             if not hasattr(d, k):
                 raise TypeError(f"unknown grid parameter {k}")
@@ -167,13 +175,18 @@ class Grid:
         return int(_lib.crn_last_launch_count(self._h))
 
     # -- calls ---------------------------------------------------------------
+    @property
+    def boundary_shape(self):
+        """(n_theta, n_phi) for B_r; (2, n_theta, n_phi) for (B_r, B_theta) with large-E."""
+        return self.shape[1:] if self.desc.inner_bc == 0 else (2,) + self.shape[1:]
+
     def set_inner_boundary(self, Br, stream=None):
-        """Prescribe B_r[n_theta, n_phi] (FP64 CUDA tensor) at the inner face centres."""
+        """Prescribe B_r (and B_theta for the large-E form) at the inner face centres."""
         import torch
         if Br.dtype != torch.float64 or not Br.is_cuda or not Br.is_contiguous():
             raise ValueError("Br must be a contiguous float64 CUDA tensor")
-        if tuple(Br.shape) != self.shape[1:]:
-            raise ValueError(f"Br must have shape {self.shape[1:]}")
+        if tuple(Br.shape) != self.boundary_shape:
+            raise ValueError(f"Br must have shape {self.boundary_shape}")
         _check(_lib.crn_set_inner_boundary(self._h, _ptr(Br), _stream_handle(stream)))
         self._br = Br
 
@@ -203,7 +216,7 @@ class Grid:
         if Ubar is None:
             Ubar = torch.empty_like(U)
         if Brbar is None and want_br:
-            Brbar = torch.empty(self.shape[1:], dtype=torch.float64, device=U.device)
+            Brbar = torch.empty(self.boundary_shape, dtype=torch.float64, device=U.device)
         _check(_lib.crn_residual_vjp(self._h, _ptr(U), _ptr(Rbar), _ptr(Ubar), _ptr(Brbar),
                                      _stream_handle(stream)))
         return Ubar, Brbar
@@ -215,6 +228,24 @@ class Grid:
         _check(_lib.crn_pseudo_time_step(self._h, _ptr(U64), int(nsteps), float(cfl),
                                          _ptr(res_log10), _stream_handle(stream)))
         return U64
+
+    def boundary_efield(self, U, E=None, stream=None):
+        """E = -V_b x B_b at the inner faces, (3, n_theta, n_phi) float64."""
+        import torch
+        self._state_check(U, "U")
+        if E is None:
+            E = torch.empty((3,) + self.shape[1:], dtype=torch.float64, device=U.device)
+        _check(_lib.crn_boundary_efield(self._h, _ptr(U), _ptr(E), _stream_handle(stream)))
+        return E
+
+    def efield(self, U, E=None, stream=None):
+        """E = -V x B of every cell, (3, n_r, n_theta, n_phi) float64 (crn_efield)."""
+        import torch
+        self._state_check(U, "U")
+        if E is None:
+            E = torch.empty((3,) + self.shape, dtype=torch.float64, device=U.device)
+        _check(_lib.crn_efield(self._h, _ptr(U), _ptr(E), _stream_handle(stream)))
+        return E
 
     def sync_status(self, stream=None):
         """Synchronise and raise CoronaError if a kernel flagged a non-physical state."""

@@ -62,21 +62,36 @@ int validate(const crn_grid_desc* d) {
     return fail(CRN_E_ARG, "outer exponents must be finite");
   if (!(finite(d->rho_b) && d->rho_b > 0.0 && finite(d->p_b) && d->p_b > 0.0))
     return fail(CRN_E_ARG, "rho_b and p_b must be > 0");
+  if (d->inner_bc != CRN_INNER_LOW_E && d->inner_bc != CRN_INNER_LARGE_E)
+    return fail(CRN_E_ARG, "unknown inner_bc");
+  if ((d->outer_vr_mass != 0 && d->outer_vr_mass != 1) ||
+      (d->outer_psi_extrap != 0 && d->outer_psi_extrap != 1) || d->reserved_ != 0)
+    return fail(CRN_E_ARG, "outer_vr_mass / outer_psi_extrap must be 0 or 1, reserved_ 0");
+  if (!finite(d->vr_star) || !finite(d->outer_bphi_exp) || !finite(d->outer_vphi_exp))
+    return fail(CRN_E_ARG, "vr_star and the outer exponents must be finite");
+  if (d->r_last != 0.0 && !(finite(d->r_last) && d->r_last > d->r_in && d->r_last < d->r_out))
+    return fail(CRN_E_ARG, "r_last must be 0 or in (r_in, r_out)");
   return CRN_OK;
 }
 
 // Host geometry in FP64 (layout documented on crn::Geo).
 struct HostGeo {
   std::vector<double> ra, rb, rv, inv_dm, inv_dp, hm, hp, grav, ar, at, av, nr, nth, nph, rhat;
-  double dtheta = 0, fa = 1, fb = 1;
+  double dtheta = 0, fa = 1, fb = 1, fbp = 1, fvr = 1, fvp = 1;
 };
 
 HostGeo build_geometry(const crn_grid_desc& d) {
   HostGeo h;
   const int nr = d.n_r, nt = d.n_theta, np = d.n_phi;
   std::vector<double> rf(nr + 1), rc(nr);
-  for (int k = 0; k <= nr; ++k) rf[k] = d.r_in * std::pow(d.r_out / d.r_in, (double)k / nr);
+  // geometric faces over M cells up to r_top; a set r_last keeps one thin
+  // outermost cell [r_last, r_out] (the mesh of Sect. 4.3)
+  const bool thin = d.r_last != 0.0;
+  const int M = thin ? nr - 1 : nr;
+  const double r_top = thin ? d.r_last : d.r_out;
+  for (int k = 0; k <= M; ++k) rf[k] = d.r_in * std::pow(r_top / d.r_in, (double)k / M);
   rf[0] = d.r_in;
+  rf[M] = r_top;
   rf[nr] = d.r_out;
   for (int k = 0; k < nr; ++k) rc[k] = 0.5 * (rf[k] + rf[k + 1]);
   const double rc_in = 2.0 * d.r_in - rc[0];            // mirrored ghost centres
@@ -142,6 +157,9 @@ HostGeo build_geometry(const crn_grid_desc& d) {
   const double rI = rc[nr - 1], rG = 2.0 * d.r_out - rI;
   h.fa = std::pow(rI / rG, d.outer_rho_exp);
   h.fb = std::pow(rI / rG, d.outer_br_exp);
+  h.fbp = std::pow(rI / rG, d.outer_bphi_exp);
+  h.fvr = d.outer_vr_mass ? std::pow(rI / rG, 2.0 - d.outer_rho_exp) : 1.0;  // V_r r^2 rho = const
+  h.fvp = std::pow(rI / rG, d.outer_vphi_exp);
   return h;
 }
 
@@ -178,7 +196,8 @@ int upload_geometry(const HostGeo& h, crn::GeoBuf<T>& out) {
 }
 
 template <class T>
-crn::Phys<T> make_phys(const crn_grid_desc& d, double fa, double fb) {
+crn::Phys<T> make_phys(const crn_grid_desc& d, const HostGeo& h) {
+  const double fa = h.fa, fb = h.fb;
   crn::Phys<T> ph;
   ph.gamma = (T)d.gamma;
   ph.gm1 = (T)(d.gamma - 1.0);
@@ -190,6 +209,12 @@ crn::Phys<T> make_phys(const crn_grid_desc& d, double fa, double fb) {
   ph.p_b = (T)d.p_b;
   ph.fa = (T)fa;
   ph.fb = (T)fb;
+  ph.fbp = (T)h.fbp;
+  ph.fvr = (T)h.fvr;
+  ph.fvp = (T)h.fvp;
+  ph.psi_out = d.outer_psi_extrap ? (T)1 : (T)-1;
+  ph.large_e = d.inner_bc == CRN_INNER_LARGE_E ? 1 : 0;
+  ph.vr_star = d.vr_star;
   return ph;
 }
 
@@ -229,6 +254,25 @@ int check_ready(const crn_grid* g) {
   return CRN_OK;
 }
 
+// as check_ready, for calls that do not read the inner boundary values
+int check_ready_u(const crn_grid* g) {
+  if (!g) return fail(CRN_E_ARG, "grid is NULL");
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != g->device) return fail(CRN_E_ARG, "the current CUDA device is not the grid's device");
+  return CRN_OK;
+}
+
+int efield(crn_grid* g, const void* U, double* E, bool volume, void* stream) {
+  int nl = 0;
+  cudaError_t e = g->d.precision == CRN_FP64
+                      ? crn::launch_efield_fp64(g, (const double*)U, E, volume, (cudaStream_t)stream, &nl)
+                      : crn::launch_efield_fp32(g, (const float*)U, E, volume, (cudaStream_t)stream, &nl);
+  g->last_launches = nl;
+  if (e != cudaSuccess) return cuda_fail(e, volume ? "crn_efield launch" : "crn_boundary_efield launch");
+  return CRN_OK;
+}
+
 }  // namespace
 
 namespace crn {
@@ -258,6 +302,8 @@ int crn_grid_desc_default(crn_grid_desc* d, int32_t n_r, int32_t n_theta, int32_
   d->outer_br_exp = 2.0;
   d->rho_b = 1.0;
   d->p_b = d->g0 / 10.0;  // isothermal wind with its sonic point at 5 R_sun
+  d->inner_bc = CRN_INNER_LOW_E;
+  d->vr_star = 1935.07 / vref;  // Wind-Predict's inner outflow (Sect. 3.2), large-E only
   return CRN_OK;
 }
 
@@ -275,8 +321,8 @@ int crn_grid_create(const crn_grid_desc* d, crn_grid** out) {
   g->shape.np = d->n_phi;
   g->shape.ncell = (int64_t)d->n_r * d->n_theta * d->n_phi;
   const HostGeo h = build_geometry(*d);
-  g->ph64 = make_phys<double>(*d, h.fa, h.fb);
-  g->ph32 = make_phys<float>(*d, h.fa, h.fb);
+  g->ph64 = make_phys<double>(*d, h);
+  g->ph32 = make_phys<float>(*d, h);
   // opt the kernels in to their shared memory, then size the tiled launch:
   // radial chunk such that all CTAs fit in one wave of resident CTAs
   e = d->precision == CRN_FP64 ? crn::prepare_fp64() : crn::prepare_fp32();
@@ -294,6 +340,7 @@ int crn_grid_create(const crn_grid_desc* d, crn_grid** out) {
       if (v >= 1) kc = v;
     }
     g->cfg.kchunk_tiled = kc;
+    g->cfg.num_sms = std::max(nsm, 1);
     const int64_t tiled_blocks = ntiles * ((d->n_r + kc - 1) / kc);
     const int64_t cell_blocks = (g->shape.ncell + 255) / 256;
     g->max_blocks = (size_t)std::max<int64_t>(std::max<int64_t>(tiled_blocks, cell_blocks), 4 * 152 * 8);
@@ -301,7 +348,7 @@ int crn_grid_create(const crn_grid_desc* d, crn_grid** out) {
   rc = upload_geometry(h, g->g64);
   if (rc == CRN_OK) rc = upload_geometry(h, g->g32);
   if (rc != CRN_OK) { free_grid(g); return rc; }
-  const size_t nt_np = (size_t)d->n_theta * d->n_phi;
+  const size_t nt_np = (size_t)d->n_theta * d->n_phi * (d->inner_bc == CRN_INNER_LARGE_E ? 2 : 1);
   const size_t n9 = (size_t)9 * g->shape.ncell;
   struct { void** p; size_t bytes; const char* what; } allocs[] = {
       {(void**)&g->br, nt_np * sizeof(double), "B_r"},
@@ -340,7 +387,8 @@ int crn_grid_destroy(crn_grid* g) {
 int crn_set_inner_boundary(crn_grid* g, const double* Br_dev, void* stream) {
   if (!g) return fail(CRN_E_ARG, "grid is NULL");
   if (!Br_dev || !is_device_ptr(Br_dev)) return fail(CRN_E_ARG, "Br_dev must be a device pointer");
-  const size_t bytes = (size_t)g->d.n_theta * g->d.n_phi * sizeof(double);
+  const size_t bytes = (size_t)g->d.n_theta * g->d.n_phi * sizeof(double) *
+                       (g->d.inner_bc == CRN_INNER_LARGE_E ? 2 : 1);
   cudaError_t e = cudaMemcpyAsync(g->br, Br_dev, bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "crn_set_inner_boundary");
   g->have_br = true;
@@ -434,6 +482,22 @@ int crn_pseudo_time_step(crn_grid* g, double* U64_dev, int32_t nsteps, double cf
   g->last_launches = total;
   if (e != cudaSuccess) return cuda_fail(e, "crn_pseudo_time_step launch");
   return CRN_OK;
+}
+
+int crn_boundary_efield(crn_grid* g, const void* U_dev, double* E_dev, void* stream) {
+  int rc = check_ready(g);
+  if (rc != CRN_OK) return rc;
+  if (!U_dev || !E_dev || !is_device_ptr(U_dev) || !is_device_ptr(E_dev))
+    return fail(CRN_E_ARG, "U_dev and E_dev must be device pointers");
+  return efield(g, U_dev, E_dev, false, stream);
+}
+
+int crn_efield(crn_grid* g, const void* U_dev, double* E_dev, void* stream) {
+  int rc = check_ready_u(g);
+  if (rc != CRN_OK) return rc;
+  if (!U_dev || !E_dev || !is_device_ptr(U_dev) || !is_device_ptr(E_dev))
+    return fail(CRN_E_ARG, "U_dev and E_dev must be device pointers");
+  return efield(g, U_dev, E_dev, true, stream);
 }
 
 int crn_sync_status(crn_grid* g, void* stream) {

@@ -21,6 +21,7 @@ struct GeoBuf {
 
 struct LaunchCfg {
   int kchunk_tiled = 16;  // radial planes per CTA of the tiled kernel
+  int num_sms = 152;      // streaming multiprocessors of the grid's device
 };
 
 }  // namespace crn
@@ -64,6 +65,10 @@ cudaError_t launch_vjp_fp64(crn_grid* g, const double* U, const double* Rb, doub
 cudaError_t launch_vjp_fp32(crn_grid* g, const float* U, const float* Rb, float* Ub, double* Brb,
                             cudaStream_t st, int* nlaunch);
 size_t vjp_scratch_bytes(const crn_grid* g);
+cudaError_t launch_efield_fp64(crn_grid* g, const double* U, double* E, bool volume, cudaStream_t st,
+                                int* nl);
+cudaError_t launch_efield_fp32(crn_grid* g, const float* U, double* E, bool volume, cudaStream_t st,
+                                int* nl);
 
 // shared-memory footprint of the tiled kernel for one precision
 size_t tiled_smem_fp64();

@@ -51,7 +51,12 @@ struct Geo {
 
 template <class T>
 struct Phys {
-  T gamma, gm1, igm1, ch, ch2, eps, rho_b, p_b, fa, fb;
+  T gamma, gm1, igm1, ch, ch2, eps, rho_b, p_b;
+  T fa, fb;        // outer ghost: rho, p and B_r factors (r_I / r_G)^a, ^b
+  T fbp, fvr, fvp; // outer ghost: B_phi, V_r and V_phi factors
+  T psi_out;       // outer ghost psi = psi_out * psi_I (-1: psi_b = 0, +1: zero-gradient)
+  int large_e;     // inner boundary: 0 low-E, 1 large-E
+  double vr_star;  // large-E prescribed radial outflow
 };
 
 struct Shape {
@@ -112,6 +117,39 @@ __device__ __forceinline__ void recover(const float (&u)[NV], const Phys<float>&
 // interior B (Neumann in B_theta, B_phi); V_b = (V_I . B_b) B_b / |B_b|^2 so
 // that V_b x B_b = 0; rho, p Dirichlet at the ghost centre; psi_b = 0
 // (Sect. 3.3).  The vector algebra runs in FP64 in both precisions.
+// Inner boundary, Sect. 3.2 "large E" (Wind-Predict): B_r and B_theta
+// prescribed, B_phi Neumann; V_b = V_par (B_r rhat + B_theta thetahat) with
+// V_par = V_r* B_r / (B_r^2 + B_theta^2), i.e. V_r = V_par B_r, V_theta =
+// V_par B_theta, V_phi = 0; rho, p Dirichlet; psi_b = 0.  FP64.
+template <class T>
+__device__ __forceinline__ void large_e_ghost(const T (&wi)[NV], double br, double bt, double ex,
+                                              double ey, double ez, const Phys<T>& ph, T (&wg)[NV]) {
+  const double st = sqrt(ex * ex + ey * ey);        // sin(theta_c) > 0 at cell centres
+  const double cp = ex / st, sp = ey / st;
+  const double et[3] = {ez * cp, ez * sp, -st};     // thetahat
+  const double ep[3] = {-sp, cp, 0.0};              // phihat
+  const double er[3] = {ex, ey, ez};
+  const double bip = (double)wi[4] * ep[0] + (double)wi[5] * ep[1];
+  const double bpol2 = br * br + bt * bt;
+  const double vpar = ph.vr_star * br / fmax(bpol2, 1e-300);
+  wg[0] = ph.rho_b;
+  wg[7] = ph.p_b;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const double pol = br * er[c] + bt * et[c];
+    wg[1 + c] = (T)(2.0 * vpar * pol - (double)wi[1 + c]);
+    wg[4 + c] = (T)(2.0 * (pol + bip * ep[c]) - (double)wi[4 + c]);
+  }
+  wg[8] = -wi[8];
+}
+
+// The prescribed boundary field is read from br_plane[col] (B_r) and, for the
+// large-E form, br_plane[nc + col] (B_theta).
+template <class T>
+__device__ __forceinline__ void inner_ghost_at(const T (&wi)[NV], const double* __restrict__ br_plane,
+                                               int64_t col, int64_t nc, double ex, double ey,
+                                               double ez, const Phys<T>& ph, T (&wg)[NV]);
+
 template <class T>
 __device__ __forceinline__ void inner_ghost(const T (&wi)[NV], double br, double ex, double ey,
                                             double ez, const Phys<T>& ph, T (&wg)[NV]) {
@@ -135,21 +173,41 @@ __device__ __forceinline__ void inner_ghost(const T (&wi)[NV], double br, double
   wg[8] = -wi[8];
 }
 
-// Outer boundary, Sect. 4.1 / Table 2: rho_G = rho_I fa, p_G = p_I fa,
-// B_r,G = B_r,I fb, tangential B and V zero-gradient, psi_b = 0, where
-// fa = (r_I/r_G)^a, fb = (r_I/r_G)^b and r_G mirrors r_I about r_out.
+template <class T>
+__device__ __forceinline__ void inner_ghost_at(const T (&wi)[NV], const double* __restrict__ br_plane,
+                                               int64_t col, int64_t nc, double ex, double ey,
+                                               double ez, const Phys<T>& ph, T (&wg)[NV]) {
+  if (ph.large_e)
+    large_e_ghost(wi, br_plane[col], br_plane[nc + col], ex, ey, ez, ph, wg);
+  else
+    inner_ghost(wi, br_plane[col], ex, ey, ez, ph, wg);
+}
+
+// Outer boundary, Sect. 4.1 / Table 2 (all nine cases) and Sect. 4.2: with
+// s = r_I / r_G (r_G mirrors r_I about r_out): rho_G = rho_I s^a, p_G = p_I s^a,
+// B_r,G = B_r,I s^b, B_phi,G = B_phi,I s^c, V_r,G = V_r,I s^(2-a) (if V_r r^2
+// rho = const) or V_r,I, V_phi,G = V_phi,I s^e; theta components
+// zero-gradient; psi_G = -psi_I (psi_b = 0) or psi_I.  The factors are in ph.
 template <class T>
 __device__ __forceinline__ void outer_ghost(const T (&wi)[NV], T ex, T ey, T ez,
                                             const Phys<T>& ph, T (&wg)[NV]) {
+  const T st = sqrt(ex * ex + ey * ey);
+  const T px = -ey / st, py = ex / st;  // phihat (z component 0)
   const T bir = wi[4] * ex + wi[5] * ey + wi[6] * ez;
-  const T dbr = bir * ph.fb - bir;
+  const T bip = wi[4] * px + wi[5] * py;
+  const T vir = wi[1] * ex + wi[2] * ey + wi[3] * ez;
+  const T vip = wi[1] * px + wi[2] * py;
+  const T dbr = bir * ph.fb - bir, dbp = bip * ph.fbp - bip;
+  const T dvr = vir * ph.fvr - vir, dvp = vip * ph.fvp - vip;
   wg[0] = wi[0] * ph.fa;
-  wg[1] = wi[1]; wg[2] = wi[2]; wg[3] = wi[3];
-  wg[4] = wi[4] + dbr * ex;
-  wg[5] = wi[5] + dbr * ey;
+  wg[1] = wi[1] + dvr * ex + dvp * px;
+  wg[2] = wi[2] + dvr * ey + dvp * py;
+  wg[3] = wi[3] + dvr * ez;
+  wg[4] = wi[4] + dbr * ex + dbp * px;
+  wg[5] = wi[5] + dbr * ey + dbp * py;
   wg[6] = wi[6] + dbr * ez;
   wg[7] = wi[7] * ph.fa;
-  wg[8] = -wi[8];
+  wg[8] = ph.psi_out * wi[8];
 }
 
 // ---------------------------------------------------------------------------

@@ -176,8 +176,8 @@ __device__ void cell_prim(const Shape& sh, const Geo<T>& g, const Phys<T>& ph,
     T wi[NV];
     load_recover(U, sh.ncell, col, ph, wi);
     const int64_t cs = (int64_t)sh.nt * sh.np;
-    inner_ghost(wi, Br[col], (double)g.rhat[col], (double)g.rhat[cs + col],
-                (double)g.rhat[2 * cs + col], ph, w);
+    inner_ghost_at(wi, Br, col, cs, (double)g.rhat[col], (double)g.rhat[cs + col],
+                   (double)g.rhat[2 * cs + col], ph, w);
   } else if (k >= sh.nr) {
     T wi[NV];
     load_recover(U, sh.ncell, (int64_t)(sh.nr - 1) * plane + col, ph, wi);
@@ -317,6 +317,49 @@ residual_cellwise(Shape sh, Geo<T> g, Phys<T> ph, const double* __restrict__ Br,
     if (!(wc[0] > (T)0) || !(wc[7] > (T)0) || !(chk <= 1.7e308)) flag_bad(red, cell);
   }
   reduce_and_finalize<256>(sq, dtmin, red, scratch);
+}
+
+// ---------------------------------------------------------------------------
+// boundary electric field diagnostic: E = -V_b x B_b of the face-mean state at
+// every inner face, in FP64 [Sect. 2.2 E = -V x B; Sect. 3.2]
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(128)
+boundary_efield_kernel(Shape sh, Geo<T> g, Phys<T> ph, const double* __restrict__ Br,
+                       const T* __restrict__ U, double* __restrict__ E) {
+  const int64_t cs = (int64_t)sh.nt * sh.np;
+  const int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= cs) return;
+  T wi[NV], wg[NV];
+  load_recover(U, sh.ncell, col, ph, wi);
+  inner_ghost_at(wi, Br, col, cs, (double)g.rhat[col], (double)g.rhat[cs + col],
+                 (double)g.rhat[2 * cs + col], ph, wg);
+  double v[3], b[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    v[c] = 0.5 * ((double)wg[1 + c] + (double)wi[1 + c]);
+    b[c] = 0.5 * ((double)wg[4 + c] + (double)wi[4 + c]);
+  }
+  E[col] = -(v[1] * b[2] - v[2] * b[1]);
+  E[cs + col] = -(v[2] * b[0] - v[0] * b[2]);
+  E[2 * cs + col] = -(v[0] * b[1] - v[1] * b[0]);
+}
+
+// cell-centred E = -V x B = -(m x B) / rho of every cell in FP64 (the volume
+// field of Sect. 3.1); E[3][ncell], one cell per thread, grid-stride.
+template <class T>
+__global__ void __launch_bounds__(256)
+cell_efield_kernel(int64_t ncell, const T* __restrict__ U, double* __restrict__ E) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += stride) {
+    const double rho = (double)U[c];
+    const double m0 = (double)U[ncell + c], m1 = (double)U[2 * ncell + c], m2 = (double)U[3 * ncell + c];
+    const double b0 = (double)U[4 * ncell + c], b1 = (double)U[5 * ncell + c], b2 = (double)U[6 * ncell + c];
+    const double v0 = m0 / rho, v1 = m1 / rho, v2 = m2 / rho;
+    E[c] = -(v1 * b2 - v2 * b1);
+    E[ncell + c] = -(v2 * b0 - v0 * b2);
+    E[2 * ncell + c] = -(v0 * b1 - v1 * b0);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -535,8 +578,8 @@ residual_tiled(Shape sh, Geo<T> g, Phys<T> ph, const double* __restrict__ Br,
     if (k0 >= 1) {
       recover(um1, ph, wm1);
     } else {
-      inner_ghost(w0, Br[ccol], (double)g.rhat[ccol], (double)g.rhat[cs + ccol],
-                  (double)g.rhat[2 * cs + ccol], ph, wm1);
+      inner_ghost_at(w0, Br, ccol, cs, (double)g.rhat[ccol], (double)g.rhat[cs + ccol],
+                     (double)g.rhat[2 * cs + ccol], ph, wm1);
     }
     if (k0 >= 2) {
       recover(um2, ph, wm2);
@@ -544,8 +587,8 @@ residual_tiled(Shape sh, Geo<T> g, Phys<T> ph, const double* __restrict__ Br,
       T wz[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) wz[v] = wm1[v];  // plane 0
-      inner_ghost(wz, Br[ccol], (double)g.rhat[ccol], (double)g.rhat[cs + ccol],
-                  (double)g.rhat[2 * cs + ccol], ph, wm2);
+      inner_ghost_at(wz, Br, ccol, cs, (double)g.rhat[ccol], (double)g.rhat[cs + ccol],
+                     (double)g.rhat[2 * cs + ccol], ph, wm2);
     }
     // r face k0 - 1/2
     T wl[NV], wr[NV], up0[NV];

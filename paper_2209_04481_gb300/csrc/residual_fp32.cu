@@ -11,4 +11,8 @@ cudaError_t launch_residual_fp32(crn_grid* g, const float* U, float* R, double* 
 size_t tiled_smem_fp32() { return tiled_smem_t<float>(); }
 cudaError_t prepare_fp32() { return prepare_t<float>(); }
 int tiled_ctas_per_sm_fp32(int limiter) { return tiled_ctas_t<float>(limiter); }
+cudaError_t launch_efield_fp32(crn_grid* g, const float* U, double* E, bool volume, cudaStream_t st,
+                                int* nl) {
+  return efield_t<float>(g, U, E, volume, st, nl);
+}
 }  // namespace crn

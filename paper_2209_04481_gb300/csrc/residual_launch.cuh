@@ -95,6 +95,21 @@ int tiled_ctas_t(int limiter) {
 }
 
 template <class T>
+cudaError_t efield_t(crn_grid* g, const T* U, double* E, bool volume, cudaStream_t st, int* nl) {
+  if (volume) {
+    const int64_t n = g->shape.ncell;
+    const int64_t nb = std::min<int64_t>((n + 255) / 256, (int64_t)g->cfg.num_sms * 8);
+    cell_efield_kernel<T><<<(unsigned)nb, 256, 0, st>>>(n, U, E);
+  } else {
+    const int64_t cs = (int64_t)g->shape.nt * g->shape.np;
+    boundary_efield_kernel<T><<<(unsigned)((cs + 127) / 128), 128, 0, st>>>(
+        g->shape, geo_of<T>(g), phys_of<T>(g), g->br, U, E);
+  }
+  *nl = 1;
+  return cudaGetLastError();
+}
+
+template <class T>
 size_t tiled_smem_t() {
   using D = TileDims<TileFor<T>::TT, TileFor<T>::TP>;
   return D::template smem_bytes<T>();

@@ -97,6 +97,14 @@ int validate_static(const crn_grid_desc* d) {
     return fail(CRN_E_ARG, "outer exponents must be finite");
   if (!(d->rho_b > 0.0 && d->p_b > 0.0 && std::isfinite(d->rho_b) && std::isfinite(d->p_b)))
     return fail(CRN_E_ARG, "rho_b and p_b must be > 0");
+  if ((d->inner_bc != CRN_INNER_LOW_E && d->inner_bc != CRN_INNER_LARGE_E) ||
+      (d->outer_vr_mass != 0 && d->outer_vr_mass != 1) ||
+      (d->outer_psi_extrap != 0 && d->outer_psi_extrap != 1) || d->reserved_ != 0)
+    return fail(CRN_E_ARG, "bad boundary-law field");
+  if (!std::isfinite(d->vr_star) || !std::isfinite(d->outer_bphi_exp) || !std::isfinite(d->outer_vphi_exp))
+    return fail(CRN_E_ARG, "vr_star and the outer exponents must be finite");
+  if (d->r_last != 0.0)
+    return fail(CRN_E_ARG, "crn_residual_static takes the geometric radial faces only (r_last = 0)");
   return CRN_OK;
 }
 
@@ -213,6 +221,12 @@ crn::Phys<T> phys_static(const crn_grid_desc& d) {
   ph.p_b = (T)d.p_b;
   ph.fa = (T)std::pow(rI / rG, d.outer_rho_exp);
   ph.fb = (T)std::pow(rI / rG, d.outer_br_exp);
+  ph.fbp = (T)std::pow(rI / rG, d.outer_bphi_exp);
+  ph.fvr = d.outer_vr_mass ? (T)std::pow(rI / rG, 2.0 - d.outer_rho_exp) : (T)1;
+  ph.fvp = (T)std::pow(rI / rG, d.outer_vphi_exp);
+  ph.psi_out = d.outer_psi_extrap ? (T)1 : (T)-1;
+  ph.large_e = d.inner_bc == CRN_INNER_LARGE_E ? 1 : 0;
+  ph.vr_star = d.vr_star;
   return ph;
 }
 

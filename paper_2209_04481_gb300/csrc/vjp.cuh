@@ -235,19 +235,63 @@ __device__ double inner_ghost_adjoint(const T (&wi)[NV], double br, double ex, d
   return Be;
 }
 
+// large-E inner ghost: cotangents to the interior primitive and to the
+// prescribed (B_r, B_theta), returned in brb[0], brb[1]
+template <class T>
+__device__ void large_e_ghost_adjoint(double br, double bt, double ex, double ey, double ez,
+                                      const Phys<T>& ph, const T (&gb)[NV], T (&wib)[NV],
+                                      double (&brb)[2]) {
+  const double st = sqrt(ex * ex + ey * ey);
+  const double cp = ex / st, sp = ey / st;
+  const double et[3] = {ez * cp, ez * sp, -st};
+  const double ep[3] = {-sp, cp, 0.0};
+  const double er[3] = {ex, ey, ez};
+  const double D = br * br + bt * bt;
+  const bool floor = !(D > 1e-300);
+  const double Dd = floor ? 1e-300 : D;
+  const double vpar = ph.vr_star * br / Dd;
+  double polb[3], vparb = 0.0, bipb = 0.0;
+  for (int c = 0; c < 3; ++c) {
+    const double vg = gb[1 + c], bg = gb[4 + c];
+    const double pol = br * er[c] + bt * et[c];
+    polb[c] = 2.0 * vpar * vg + 2.0 * bg;
+    vparb += 2.0 * vg * pol;
+    bipb += 2.0 * bg * ep[c];
+    wib[1 + c] -= (T)vg;
+    wib[4 + c] -= (T)bg;
+  }
+  wib[8] -= gb[8];
+  for (int c = 0; c < 3; ++c) wib[4 + c] += (T)(bipb * ep[c]);
+  brb[0] = polb[0] * er[0] + polb[1] * er[1] + polb[2] * er[2];
+  brb[1] = polb[0] * et[0] + polb[1] * et[1] + polb[2] * et[2];
+  // V_par = vr* B_r / D, D = B_r^2 + B_theta^2
+  if (floor) {
+    brb[0] += vparb * ph.vr_star / Dd;
+  } else {
+    brb[0] += vparb * (ph.vr_star / D - 2.0 * ph.vr_star * br * br / (D * D));
+    brb[1] += vparb * (-2.0 * ph.vr_star * br * bt / (D * D));
+  }
+}
+
+// generalized outer ghost (Table 2 laws): the ghost is a fixed linear map of
+// the interior primitive state
 template <class T>
 __device__ __forceinline__ void outer_ghost_adjoint(T ex, T ey, T ez, const Phys<T>& ph,
                                                     const T (&gb)[NV], T (&wib)[NV]) {
+  const T st = sqrt(ex * ex + ey * ey);
+  const T px = -ey / st, py = ex / st;
   const T e[3] = {ex, ey, ez};
+  const T pe[3] = {px, py, (T)0};
   wib[0] += ph.fa * gb[0];
   wib[7] += ph.fa * gb[7];
-  const T ge = gb[4] * ex + gb[5] * ey + gb[6] * ez;
+  const T bre = gb[4] * ex + gb[5] * ey + gb[6] * ez, bpe = gb[4] * px + gb[5] * py;
+  const T vre = gb[1] * ex + gb[2] * ey + gb[3] * ez, vpe = gb[1] * px + gb[2] * py;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    wib[1 + c] += gb[1 + c];
-    wib[4 + c] += gb[4 + c] + (ph.fb - (T)1) * ge * e[c];
+    wib[1 + c] += gb[1 + c] + (ph.fvr - (T)1) * vre * e[c] + (ph.fvp - (T)1) * vpe * pe[c];
+    wib[4 + c] += gb[4 + c] + (ph.fb - (T)1) * bre * e[c] + (ph.fbp - (T)1) * bpe * pe[c];
   }
-  wib[8] -= gb[8];
+  wib[8] += ph.psi_out * gb[8];
 }
 
 // U -> W recovery adjoint (plain, no low-beta island: derivatives only)
@@ -472,9 +516,15 @@ vjp_cells(Shape sh, Geo<T> g, Phys<T> ph, const double* __restrict__ Br, const T
   for (int v = 0; v < NV; ++v) u[v] = U[v * N + c];
   recover(u, ph, w);
   if (k == 0) {
-    const double brb = inner_ghost_adjoint(w, Br[col], (double)g.rhat[col], (double)g.rhat[cs + col],
-                                           (double)g.rhat[2 * cs + col], gin, wb);
-    if (Brb) Brb[col] = brb;
+    const double ex = g.rhat[col], ey = g.rhat[cs + col], ez = g.rhat[2 * cs + col];
+    if (ph.large_e) {
+      double brb[2];
+      large_e_ghost_adjoint(Br[col], Br[cs + col], ex, ey, ez, ph, gin, wb, brb);
+      if (Brb) { Brb[col] = brb[0]; Brb[cs + col] = brb[1]; }
+    } else {
+      const double brb = inner_ghost_adjoint(w, Br[col], ex, ey, ez, gin, wb);
+      if (Brb) Brb[col] = brb;
+    }
   }
   if (k == nr - 1) outer_ghost_adjoint(g.rhat[col], g.rhat[cs + col], g.rhat[2 * cs + col], ph, gout, wb);
   // ---- recovery and gravity source

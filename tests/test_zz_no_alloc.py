@@ -78,3 +78,17 @@ def test_static_entry_point_rejects_oversized_grids():
                                  None, None, None)
     assert rc == 1
     assert "32768" in lib.crn_last_error().decode()
+
+
+def test_static_entry_point_rejects_thin_last_cell():
+    """The thin-outer-cell mesh (r_last != 0) is a crn_grid_create option only."""
+    pg, lib = _lib()
+    d = pg.GridDesc()
+    lib.crn_grid_desc_default(ctypes.byref(d), 8, 8, 32)
+    d.r_out, d.r_last = 25.0, 24.95
+    x = torch.zeros(9 * 8 * 8 * 32, dtype=torch.float32, device="cuda")
+    br = torch.zeros(8 * 32, dtype=torch.float64, device="cuda")
+    rc = lib.crn_residual_static(ctypes.byref(d), _p(br), _p(x), _p(torch.empty_like(x)),
+                                 None, None, None)
+    assert rc == 1
+    assert "r_last" in lib.crn_last_error().decode()
