@@ -58,10 +58,13 @@ typedef enum { CRN_FP64 = 0, CRN_FP32_BULK = 1 } crn_precision;
 typedef enum { CRN_LIM_NONE = 0, CRN_LIM_MINMOD = 1, CRN_LIM_VANALBADA = 2 } crn_limiter;
 typedef enum { CRN_KERNEL_TILED = 0, CRN_KERNEL_CELLWISE = 1 } crn_kernel;
 /* Inner-boundary formulation (Sect. 3.2): LOW_E: B_r prescribed, B_theta and
- * B_phi Neumann, V_b parallel to B_b (E_b = 0).  LARGE_E: the Wind-Predict
- * form, B_r and B_theta prescribed (from a potential field), B_phi Neumann,
- * V_b = V_par (B_r rhat + B_theta thetahat), V_par = V_r* B_r / B_pol^2. */
-typedef enum { CRN_INNER_LOW_E = 0, CRN_INNER_LARGE_E = 1 } crn_inner_bc;
+ * B_phi Neumann, V_b parallel to B_b (E_b = 0), |V_b| from the interior
+ * velocity projected on B_b.  LARGE_E: the Wind-Predict form, B_r and B_theta
+ * prescribed (from a potential field), B_phi Neumann, V_b = V_par (B_r rhat +
+ * B_theta thetahat), V_par = V_r* B_r / B_pol^2.  LOW_E_WP: as LOW_E but with
+ * the prescribed Wind-Predict outflow magnitude, V_b = V_r* B_r B_b / |B_b|^2
+ * (E_b = 0; V_b does not depend on the interior velocity). */
+typedef enum { CRN_INNER_LOW_E = 0, CRN_INNER_LARGE_E = 1, CRN_INNER_LOW_E_WP = 2 } crn_inner_bc;
 
 /* Grid and physics description.  crn_grid_desc_default fills the solar-wind
  * defaults: r in [1, 21.5], gamma = 1.05, c_h = 1, g0 = 0.8271 (G M_sun /

@@ -86,6 +86,8 @@ def _load():
             lib.orc_boundary_efield.restype = ctypes.c_int
             lib.orc_efield.argtypes = [D, P, P]
             lib.orc_efield.restype = ctypes.c_int
+            lib.orc_local_dt.argtypes = [D, P, P]
+            lib.orc_local_dt.restype = ctypes.c_int
             lib.orc_pseudo_time_step.argtypes = [D, P, P, ctypes.c_int, ctypes.c_double, P, P]
             for f in (lib.orc_residual, lib.orc_residual_jvp, lib.orc_flux, lib.orc_cons_to_prim,
                       lib.orc_geometry, lib.orc_ghosts, lib.orc_pseudo_time_step):
@@ -116,7 +118,7 @@ class Grid:
     outer_br_exp: float = 2.0
     rho_b: float = 1.0
     p_b: float = 0.0
-    inner_bc: str = "low_e"          # "low_e" | "large_e"
+    inner_bc: str = "low_e"          # "low_e" | "large_e" | "low_e_wp"
     vr_star: float = 0.0
     outer_bphi_exp: float = 0.0
     outer_vphi_exp: float = 0.0
@@ -148,7 +150,7 @@ class Grid:
         d.gamma, d.c_h, d.g0 = self.gamma, self.c_h, self.g0
         d.outer_rho_exp, d.outer_br_exp = self.outer_rho_exp, self.outer_br_exp
         d.rho_b, d.p_b = self.rho_b, self.p_b
-        d.inner_bc = {"low_e": 0, "large_e": 1}[self.inner_bc]
+        d.inner_bc = {"low_e": 0, "large_e": 1, "low_e_wp": 2}[self.inner_bc]
         d.outer_vr_mass = int(bool(self.outer_vr_mass))
         d.outer_psi_extrap = int(bool(self.outer_psi_extrap))
         d.vr_star = self.vr_star
@@ -289,6 +291,65 @@ def pseudo_time_step(grid: Grid, U, Br, nsteps: int, cfl: float):
                                 _ptr(res), _ptr(dts)):
         raise ValueError("bad description")
     return U, res[:nsteps], dts[:nsteps]
+
+
+def local_dt(grid: Grid, U):
+    """Local pseudo-time step dt_c = V_c / sum_f max(|V.n_f| + c_f, c_h)|S_f| of
+    every cell from its own state, shape (n0, n1, n2)."""
+    lib = _load()
+    U = _f64(U, (9,) + grid.shape)
+    dt = np.empty(grid.shape)
+    if lib.orc_local_dt(ctypes.byref(grid.desc()), _ptr(U), _ptr(dt)):
+        raise ValueError("bad description")
+    return dt
+
+
+def jacobian(grid: Grid, U, Br=None):
+    """Dense dR/dU (9N x 9N, state flattened in SoA order), column by column
+    from the dual-number JVP; for grids of a few hundred cells."""
+    n = 9 * grid.ncell
+    J = np.empty((n, n))
+    e = np.zeros(n)
+    dB = None if Br is None else np.zeros(np.shape(Br))
+    for c in range(n):
+        e[c] = 1.0
+        J[:, c] = residual_jvp(grid, U, Br, e.reshape((9,) + grid.shape), dB)[1].ravel()
+        e[c] = 0.0
+    return J
+
+
+def backward_euler_step(grid: Grid, U, Br, cfl, solver="dense", rtol=1e-12, J=None):
+    """One step of the implicit pseudo-time iteration of Sect. 2.1 (backward
+    Euler, linearised once, local time steps): the solution dU of
+
+        (diag(1 / (cfl dt_c)) - dR/dU) dU = R(U),
+
+    dt_c from ``local_dt`` (shared by the nine variables of a cell), J = dR/dU
+    exact (dual numbers).  cfl = inf gives the Newton step.  solver "dense"
+    assembles J and solves directly; "gmres" runs scipy's GMRES on the
+    dual-number JVP to ``rtol``.  Returns (dU, R)."""
+    U = _f64(U, (9,) + grid.shape)
+    R = residual(grid, U, Br)["R"]
+    dtau = cfl * local_dt(grid, U)
+    diag = np.broadcast_to(1.0 / dtau, U.shape).ravel()
+    if solver == "dense":
+        if J is None:
+            J = jacobian(grid, U, Br)
+        dU = np.linalg.solve(np.diag(diag) - J, R.ravel())
+    else:
+        from scipy.sparse.linalg import LinearOperator, gmres
+        dB = None if Br is None else np.zeros(np.shape(Br))
+
+        def apply(x):
+            jv = residual_jvp(grid, U, Br, x.reshape(U.shape), dB)[1].ravel()
+            return diag * x - jv
+
+        n = U.size
+        A = LinearOperator((n, n), matvec=apply, dtype=np.float64)
+        dU, info = gmres(A, R.ravel(), rtol=rtol, atol=0.0, restart=200, maxiter=50)
+        if info != 0:
+            raise RuntimeError(f"GMRES did not reach rtol {rtol} (info {info})")
+    return dU.reshape(U.shape), R
 
 
 def efield(grid: Grid, U):

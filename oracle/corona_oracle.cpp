@@ -105,7 +105,8 @@ typedef struct {
   double outer_rho_exp;    // outer ghost: rho, p scaled by (r_I/r_G)^a
   double outer_br_exp;     // outer ghost: B_r scaled by (r_I/r_G)^b
   double rho_b, p_b;       // inner boundary density and pressure
-  int32_t inner_bc;        // 0 low-E (Sect. 3.2), 1 large-E / Wind-Predict (Sect. 3.2)
+  int32_t inner_bc;        // 0 low-E, 1 large-E (Wind-Predict), 2 low-E with the
+                           // Wind-Predict outflow magnitude (all Sect. 3.2)
   int32_t outer_vr_mass;   // outer ghost V_r: 0 zero-gradient, 1 V_r r^2 rho = const
   int32_t outer_psi_extrap;// outer ghost psi: 0 psi_b = 0, 1 zero-gradient (G = I)
   int32_t pad_;
@@ -367,7 +368,10 @@ void inner_ghost(const Mesh& m, int j, int i, const T wi[9], T br, T bt, T wg[9]
   T bb2 = bb[0] * bb[0] + bb[1] * bb[1] + bb[2] * bb[2];
   T vdotb = vi[0] * bb[0] + vi[1] * bb[1] + vi[2] * bb[2];
   T den = vmax(bb2, T(1e-300));
-  for (int c = 0; c < 3; ++c) vb[c] = vdotb * bb[c] / den;
+  // low-E: |V_b| from the interior velocity projected on B_b; low-E with the
+  // Wind-Predict outflow magnitude: V_b = V_r* B_r B_b / |B_b|^2
+  T q = m.d.inner_bc == 2 ? T(m.d.vr_star) * br / den : vdotb / den;
+  for (int c = 0; c < 3; ++c) vb[c] = q * bb[c];
   wg[W_RHO] = T(m.d.rho_b);
   wg[W_P] = T(m.d.p_b);
   for (int c = 0; c < 3; ++c) {
@@ -774,6 +778,42 @@ int orc_efield(const orc_desc* d, const double* U, double* E) {
     E[1 * m.ncell + c] = -(V[2] * B[0] - V[0] * B[2]);
     E[2 * m.ncell + c] = -(V[0] * B[1] - V[1] * B[0]);
   }
+  return 0;
+}
+
+// Local pseudo-time step of every cell for the backward-Euler pseudo-time
+// iteration of Sect. 2.1 (local time stepping):
+//   dt_c = V_c / sum_f max(|V_c.n_f| + c_f(W_c, n_f), c_h) |S_f|
+// over the six faces of the cell, with the cell's own primitive state W_c on
+// every face (pole faces have zero area and drop out).  dt [n0][n1][n2].
+int orc_local_dt(const orc_desc* d, const double* U, double* dt) {
+  if (!desc_ok(d) || !U || !dt) return 1;
+  Mesh m(*d);
+  const double ch = d->c_h;
+  for (int a = 0; a < m.n[0]; ++a)
+    for (int b = 0; b < m.n[1]; ++b)
+      for (int c = 0; c < m.n[2]; ++c) {
+        const long id = m.idx(a, b, c);
+        double u[9], w[9];
+        for (int v = 0; v < 9; ++v) u[v] = U[v * m.ncell + id];
+        cons_to_prim(u, d->gamma, w);
+        const int ijk[3] = {a, b, c};
+        double sum = 0.0;
+        for (int ax = 0; ax < 3; ++ax) {
+          const int o1 = ijk[ax == 0 ? 1 : 0], o2 = ijk[ax == 2 ? 1 : 2];
+          for (int side = 0; side < 2; ++side) {
+            double S[3];
+            m.face_vector(ax, ijk[ax] + side, o1, o2, S);
+            const double area = std::sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
+            if (area == 0.0) continue;
+            const double n[3] = {S[0] / area, S[1] / area, S[2] / area};
+            double f[9], uu[9], speed;
+            physical_flux(w, n, d->gamma, ch, f, uu, speed);
+            sum += std::max(speed, ch) * area;
+          }
+        }
+        dt[id] = m.volume(a, b, c) / sum;
+      }
   return 0;
 }
 

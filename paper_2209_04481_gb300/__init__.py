@@ -139,7 +139,7 @@ class Grid:
         d.limiter = LIMITERS[limiter]
         d.kernel = {"tiled": KERNEL_TILED, "cellwise": KERNEL_CELLWISE}[kernel]
         if "inner_bc" in kw and isinstance(kw["inner_bc"], str):
-            kw["inner_bc"] = {"low_e": 0, "large_e": 1}[kw["inner_bc"]]
+            kw["inner_bc"] = {"low_e": 0, "large_e": 1, "low_e_wp": 2}[kw["inner_bc"]]
         for k, v in kw.items():
             if not hasattr(d, k):
                 raise TypeError(f"unknown grid parameter {k}")
@@ -178,7 +178,7 @@ class Grid:
     @property
     def boundary_shape(self):
         """(n_theta, n_phi) for B_r; (2, n_theta, n_phi) for (B_r, B_theta) with large-E."""
-        return self.shape[1:] if self.desc.inner_bc == 0 else (2,) + self.shape[1:]
+        return (2,) + self.shape[1:] if self.desc.inner_bc == 1 else self.shape[1:]
 
     def set_inner_boundary(self, Br, stream=None):
         """Prescribe B_r (and B_theta for the large-E form) at the inner face centres."""

@@ -62,7 +62,7 @@ int validate(const crn_grid_desc* d) {
     return fail(CRN_E_ARG, "outer exponents must be finite");
   if (!(finite(d->rho_b) && d->rho_b > 0.0 && finite(d->p_b) && d->p_b > 0.0))
     return fail(CRN_E_ARG, "rho_b and p_b must be > 0");
-  if (d->inner_bc != CRN_INNER_LOW_E && d->inner_bc != CRN_INNER_LARGE_E)
+  if (d->inner_bc < CRN_INNER_LOW_E || d->inner_bc > CRN_INNER_LOW_E_WP)
     return fail(CRN_E_ARG, "unknown inner_bc");
   if ((d->outer_vr_mass != 0 && d->outer_vr_mass != 1) ||
       (d->outer_psi_extrap != 0 && d->outer_psi_extrap != 1) || d->reserved_ != 0)
@@ -213,7 +213,7 @@ crn::Phys<T> make_phys(const crn_grid_desc& d, const HostGeo& h) {
   ph.fvr = (T)h.fvr;
   ph.fvp = (T)h.fvp;
   ph.psi_out = d.outer_psi_extrap ? (T)1 : (T)-1;
-  ph.large_e = d.inner_bc == CRN_INNER_LARGE_E ? 1 : 0;
+  ph.inner_bc = d.inner_bc;
   ph.vr_star = d.vr_star;
   return ph;
 }

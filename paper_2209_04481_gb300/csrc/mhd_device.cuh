@@ -55,7 +55,7 @@ struct Phys {
   T fa, fb;        // outer ghost: rho, p and B_r factors (r_I / r_G)^a, ^b
   T fbp, fvr, fvp; // outer ghost: B_phi, V_r and V_phi factors
   T psi_out;       // outer ghost psi = psi_out * psi_I (-1: psi_b = 0, +1: zero-gradient)
-  int large_e;     // inner boundary: 0 low-E, 1 large-E
+  int inner_bc;    // inner boundary: 0 low-E, 1 large-E, 2 low-E with the V_r* magnitude
   double vr_star;  // large-E prescribed radial outflow
 };
 
@@ -160,8 +160,10 @@ __device__ __forceinline__ void inner_ghost(const T (&wi)[NV], double br, double
   const double bby = br * ey + (biy - bir * ey);
   const double bbz = br * ez + (biz - bir * ez);
   const double bb2 = bbx * bbx + bby * bby + bbz * bbz;
-  const double vdb = vix * bbx + viy * bby + viz * bbz;
-  const double s = vdb / fmax(bb2, 1e-300);
+  // V_b = s B_b: s from the interior velocity (low-E) or from the prescribed
+  // outflow, s = V_r* B_r / |B_b|^2 (low-E with the Wind-Predict magnitude)
+  const double s = ph.inner_bc == 2 ? ph.vr_star * br / fmax(bb2, 1e-300)
+                                    : (vix * bbx + viy * bby + viz * bbz) / fmax(bb2, 1e-300);
   wg[0] = ph.rho_b;
   wg[1] = (T)(2.0 * s * bbx - vix);
   wg[2] = (T)(2.0 * s * bby - viy);
@@ -177,7 +179,7 @@ template <class T>
 __device__ __forceinline__ void inner_ghost_at(const T (&wi)[NV], const double* __restrict__ br_plane,
                                                int64_t col, int64_t nc, double ex, double ey,
                                                double ez, const Phys<T>& ph, T (&wg)[NV]) {
-  if (ph.large_e)
+  if (ph.inner_bc == 1)
     large_e_ghost(wi, br_plane[col], br_plane[nc + col], ex, ey, ez, ph, wg);
   else
     inner_ghost(wi, br_plane[col], ex, ey, ez, ph, wg);

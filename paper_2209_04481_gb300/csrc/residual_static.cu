@@ -97,7 +97,7 @@ int validate_static(const crn_grid_desc* d) {
     return fail(CRN_E_ARG, "outer exponents must be finite");
   if (!(d->rho_b > 0.0 && d->p_b > 0.0 && std::isfinite(d->rho_b) && std::isfinite(d->p_b)))
     return fail(CRN_E_ARG, "rho_b and p_b must be > 0");
-  if ((d->inner_bc != CRN_INNER_LOW_E && d->inner_bc != CRN_INNER_LARGE_E) ||
+  if ((d->inner_bc < CRN_INNER_LOW_E || d->inner_bc > CRN_INNER_LOW_E_WP) ||
       (d->outer_vr_mass != 0 && d->outer_vr_mass != 1) ||
       (d->outer_psi_extrap != 0 && d->outer_psi_extrap != 1) || d->reserved_ != 0)
     return fail(CRN_E_ARG, "bad boundary-law field");
@@ -225,7 +225,7 @@ crn::Phys<T> phys_static(const crn_grid_desc& d) {
   ph.fvr = d.outer_vr_mass ? (T)std::pow(rI / rG, 2.0 - d.outer_rho_exp) : (T)1;
   ph.fvp = (T)std::pow(rI / rG, d.outer_vphi_exp);
   ph.psi_out = d.outer_psi_extrap ? (T)1 : (T)-1;
-  ph.large_e = d.inner_bc == CRN_INNER_LARGE_E ? 1 : 0;
+  ph.inner_bc = d.inner_bc;
   ph.vr_star = d.vr_star;
   return ph;
 }

@@ -200,7 +200,7 @@ __device__ void rusanov_adjoint(const T (&wl)[NV], const T (&wr)[NV], T nx, T ny
 // primitive's cotangent wib and return the cotangent of the prescribed B_r
 template <class T>
 __device__ double inner_ghost_adjoint(const T (&wi)[NV], double br, double ex, double ey, double ez,
-                                      const T (&gb)[NV], T (&wib)[NV]) {
+                                      const Phys<T>& ph, const T (&gb)[NV], T (&wib)[NV]) {
   const double e[3] = {ex, ey, ez};
   const double bi[3] = {wi[4], wi[5], wi[6]};
   const double vi[3] = {wi[1], wi[2], wi[3]};
@@ -208,10 +208,11 @@ __device__ double inner_ghost_adjoint(const T (&wi)[NV], double br, double ex, d
   double bbd[3];
   for (int c = 0; c < 3; ++c) bbd[c] = br * e[c] + (bi[c] - bir * e[c]);
   const double bb2 = bbd[0] * bbd[0] + bbd[1] * bbd[1] + bbd[2] * bbd[2];
-  const double vdb = vi[0] * bbd[0] + vi[1] * bbd[1] + vi[2] * bbd[2];
+  const bool wp = ph.inner_bc == 2;
+  const double num = wp ? ph.vr_star * br : vi[0] * bbd[0] + vi[1] * bbd[1] + vi[2] * bbd[2];
   const bool floor = !(bb2 > 1e-300);
   const double den = floor ? 1e-300 : bb2;
-  const double s = vdb / den;
+  const double s = num / den;
   // ghost: V_g = 2 s B_b - V_I, B_g = 2 B_b - B_I, psi_g = -psi_I (rho, p fixed)
   double Bbb[3], sb = 0.0;
   for (int c = 0; c < 3; ++c) {
@@ -222,17 +223,23 @@ __device__ double inner_ghost_adjoint(const T (&wi)[NV], double br, double ex, d
     wib[4 + c] -= (T)bgb;
   }
   wib[8] -= gb[8];
-  // s = vdb / den
-  const double vdbb = sb / den;
+  // s = num / den; num = V_I . B_b (low-E) or V_r* B_r (Wind-Predict magnitude)
+  const double numb = sb / den;
   const double bb2b = floor ? 0.0 : -sb * s / den;
-  for (int c = 0; c < 3; ++c) {
-    wib[1 + c] += (T)(vdbb * bbd[c]);
-    Bbb[c] += vdbb * vi[c] + 2.0 * bb2b * bbd[c];
+  double brb = 0.0;
+  for (int c = 0; c < 3; ++c) Bbb[c] += 2.0 * bb2b * bbd[c];
+  if (wp) {
+    brb = numb * ph.vr_star;
+  } else {
+    for (int c = 0; c < 3; ++c) {
+      wib[1 + c] += (T)(numb * bbd[c]);
+      Bbb[c] += numb * vi[c];
+    }
   }
   // B_b = B_r e + B_I - (B_I . e) e
   const double Be = Bbb[0] * ex + Bbb[1] * ey + Bbb[2] * ez;
   for (int c = 0; c < 3; ++c) wib[4 + c] += (T)(Bbb[c] - Be * e[c]);
-  return Be;
+  return brb + Be;
 }
 
 // large-E inner ghost: cotangents to the interior primitive and to the
@@ -517,12 +524,12 @@ vjp_cells(Shape sh, Geo<T> g, Phys<T> ph, const double* __restrict__ Br, const T
   recover(u, ph, w);
   if (k == 0) {
     const double ex = g.rhat[col], ey = g.rhat[cs + col], ez = g.rhat[2 * cs + col];
-    if (ph.large_e) {
+    if (ph.inner_bc == 1) {
       double brb[2];
       large_e_ghost_adjoint(Br[col], Br[cs + col], ex, ey, ez, ph, gin, wb, brb);
       if (Brb) { Brb[col] = brb[0]; Brb[cs + col] = brb[1]; }
     } else {
-      const double brb = inner_ghost_adjoint(w, Br[col], ex, ey, ez, gin, wb);
+      const double brb = inner_ghost_adjoint(w, Br[col], ex, ey, ez, ph, gin, wb);
       if (Brb) Brb[col] = brb;
     }
   }

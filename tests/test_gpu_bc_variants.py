@@ -32,6 +32,8 @@ VARIANTS = {f"case{c}": table2_params(str(c)) for c in range(1, 10)}
 VARIANTS["r-2.5"] = dict(outer_rho_exp=2.5)
 VARIANTS["large_e"] = dict(inner_bc="large_e", vr_star=VR_STAR)
 VARIANTS["large_e+case9"] = dict(inner_bc="large_e", vr_star=VR_STAR, **table2_params("9"))
+VARIANTS["low_e_wp"] = dict(inner_bc="low_e_wp", vr_star=VR_STAR)
+VARIANTS["low_e_wp+case9"] = dict(inner_bc="low_e_wp", vr_star=VR_STAR, **table2_params("9"))
 # the Sect. 4.3 mesh: domain to 25 R_sun with a thin outermost cell
 VARIANTS["thin_last+case1"] = dict(r_out=25.0, r_last=24.95, **table2_params("1"))
 VARIANTS["thin_last+case9"] = dict(r_out=25.0, r_last=24.95, **table2_params("9"))
@@ -114,7 +116,7 @@ def test_boundary_efield(variant, precision):
         assert np.max(np.abs(E)) <= tol * scale
 
 
-@pytest.mark.parametrize("variant", ["large_e", "case9", "case5", "large_e+case9"])
+@pytest.mark.parametrize("variant", ["large_e", "case9", "case5", "large_e+case9", "low_e_wp", "low_e_wp+case9"])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
 def test_vjp_dot_product(variant, precision, tol):
     """<Rbar, J v> (oracle dual numbers) = <J^T Rbar, v> (GPU VJP), including

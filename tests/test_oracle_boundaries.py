@@ -11,7 +11,7 @@ import pytest
 
 import coronal_inputs as ci
 import oracle
-from _util import oracle_grid
+from _util import oracle_grid, problem
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -156,13 +156,13 @@ def test_potential_field_generator():
     np.testing.assert_allclose(num, -6 * c20 * np.cos(T) * np.sin(T), atol=1e-8)
 
 
-@pytest.mark.parametrize("variant", ["large_e", "case9"])
+@pytest.mark.parametrize("variant", ["large_e", "case9", "low_e_wp"])
 def test_jvp_of_boundary_variants(variant):
     """The dual-number JVP through the new ghost maps against central
     differences (unlimited reconstruction, h = 1e-8; B_r and B_theta perturbed)."""
     kw = dict(limiter="none", r_out=3.0)
-    if variant == "large_e":
-        kw.update(inner_bc="large_e", vr_star=1935.07 / ci.V_REF)
+    if variant in ("large_e", "low_e_wp"):
+        kw.update(inner_bc=variant, vr_star=1935.07 / ci.V_REF)
     else:
         kw.update(laws_to_params(table2()["9"]))
     g = oracle_grid((6, 6, 8), **kw)
@@ -229,3 +229,53 @@ def test_volume_efield_closed_form():
     assert np.max(np.linalg.norm(E0, axis=0) / scale) < 1e-14
     # same speed, same density: only the direction of V changed
     np.testing.assert_allclose(np.linalg.norm(W0[1:4], axis=0), v, rtol=1e-14)
+
+
+def test_low_e_wind_predict_magnitude_equations():
+    """Low-E with the Wind-Predict outflow magnitude: face-mean V_b = V_r* B_r
+    B_b / |B_b|^2 with B_b = B_r rhat + tangential interior B, so V_b x B_b = 0,
+    V_b . rhat = V_r* B_r^2 / |B_b|^2, and V_b does not move with V_I."""
+    vr_star = 1935.07 / ci.V_REF
+    shape = (4, 12, 16)
+    g = oracle_grid(shape, inner_bc="low_e_wp", vr_star=vr_star)
+    U, info = ci.background(*shape)
+    U = ci.perturb(info["W"], seed=8, amp=0.2)
+    Br = ci.magnetogram(12, 16, lmax=6, seed=5)
+    Win, _ = oracle.ghosts(g, U, Br)
+    WI = oracle.cons_to_prim(g, U)[:, 0]
+    V, B, _ = spherical(0.5 * (Win + WI), g)
+    _, BI, _ = spherical(WI, g)
+    np.testing.assert_allclose(B["r"], Br, atol=1e-14)
+    np.testing.assert_allclose(B["t"], BI["t"], atol=1e-14)
+    np.testing.assert_allclose(B["p"], BI["p"], atol=1e-14)
+    b2 = B["r"] ** 2 + B["t"] ** 2 + B["p"] ** 2
+    q = vr_star * Br / b2
+    for c in "rtp":
+        np.testing.assert_allclose(V[c], q * B[c], rtol=1e-12, atol=1e-18)
+    def face_v(W):
+        Ux = ci.prim_to_cons(W)
+        return 0.5 * (oracle.ghosts(g, Ux, Br)[0][1:4] + oracle.cons_to_prim(g, Ux)[1:4, 0])
+    W2 = info["W"].copy()
+    W2[1:4] *= 1.7
+    np.testing.assert_allclose(face_v(W2), face_v(info["W"]), rtol=1e-12, atol=1e-18)
+
+
+def test_inner_boundary_growing_mode():
+    """On the Parker + dipole state the low-E ghost with the interior-projected
+    |V_b| gives the semi-discrete operator a growing mode at the inner layer
+    (an eigenvalue of diag(dt_c) dR/dU with real part near +1, i.e. growth on
+    the local time-step scale, mostly in the energy); the large-E ghost and
+    the low-E ghost with the prescribed V_r* magnitude have none.  This is why
+    the backward-Euler iteration of Sect. 2.1 diverges with the former."""
+    shape = (4, 4, 8)
+    U, Br = problem(shape)
+    top = {}
+    for bc in ("low_e", "large_e", "low_e_wp"):
+        kw = {} if bc == "low_e" else dict(inner_bc=bc, vr_star=1935.07 / ci.V_REF)
+        g = oracle_grid(shape, **kw)
+        B = ci.potential_field(4, 8, dipole_only=True) if bc == "large_e" else Br
+        J = oracle.jacobian(g, U, B)
+        dt = np.broadcast_to(oracle.local_dt(g, U), U.shape).ravel()
+        top[bc] = np.linalg.eigvals(J * dt[:, None]).real.max()
+    assert top["low_e"] > 0.5
+    assert top["large_e"] < 0.0 and top["low_e_wp"] < 0.0
