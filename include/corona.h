@@ -206,6 +206,84 @@ int crn_boundary_efield(crn_grid* g, const void* U_dev, double* E_dev, void* str
  * boundary values.  Asynchronous on `stream`; one launch. */
 int crn_efield(crn_grid* g, const void* U_dev, double* E_dev, void* stream);
 
+/* ---- implicit pseudo-time iteration: matrix-free Newton-Krylov ----------
+ * The backward-Euler pseudo-time step of Sect. 2.1 with local time steps,
+ * linearised once:  (diag(1 / dtau_c) - dR/dU) dU = R(U),  dtau_c = CFL dt_c,
+ *   dt_c = V_c / sum_f max(|V_c.n_f| + c_f(W_c, n_f), c_h) |S_f|
+ * (the cell's own state on its six faces; pole faces drop out), solved by
+ * restarted GMRES on y -> y - J(dtau . y), dU = dtau . y.  J z is the
+ * central difference (R(U + eps z) - R(U - eps z)) / (2 eps) of two
+ * crn_residual evaluations (or the forward difference against R(U)), eps the
+ * largest step that moves no state entry by more than fd_rel of |u| + 1e-3 x
+ * (the mean |u| of its variable + the mean |u| over all nine variables) and no
+ * cell's linearised pressure by more than a quarter.  U is then advanced by alpha dU, alpha = min(1,
+ * max_rel_change / max_c max(|d rho|/rho, |dp_lin|/p)) (dp_lin the linearised
+ * pressure change), halved while any cell would get rho <= 0 or p <= 0.
+ * All vectors are FP64 on the device; reductions are deterministic. */
+typedef struct {
+  int32_t krylov_dim;      /* GMRES restart length m, 1..500 (default 30)          */
+  int32_t max_restarts;    /* GMRES restarts per step, 0..1000 (default 0)          */
+  double lin_rtol;         /* GMRES relative tolerance, (0, 1) (default 1e-3)       */
+  double fd_rel;           /* relative FD step b; 0 selects 2^-17 (central) or 2^-26
+                              (forward) on FP64 grids, 2^-8 or 2^-12 on FP32-bulk
+                              grids (default 0)                                     */
+  double max_rel_change;   /* step limiter omega; <= 0 disables it (default 0.3)    */
+  int32_t fd_central;      /* 1: central difference (two residuals per product),
+                              0: forward difference (default 1)                     */
+  int32_t reserved_;       /* 0                                                     */
+} crn_nk_options;
+
+typedef struct {
+  double res_l2;           /* ||R(U)||_2 over all 9N entries before the step        */
+  double lin_rel;          /* GMRES relative residual estimate at exit              */
+  double alpha;            /* step length applied                                   */
+  int32_t krylov_iters;    /* Arnoldi steps (one Jacobian-vector product each)      */
+  int32_t residual_evals;  /* residual evaluations of the step                      */
+} crn_nk_stats;
+
+/* The CFL law of Sect. 4.1: cfl0 (2), doubled every cfl_double_every steps
+ * up to cfl_max (128). */
+typedef struct {
+  double cfl0, cfl_max;
+  int32_t cfl_double_every;  /* default 10                                          */
+  int32_t max_steps;         /* default 500                                         */
+  double tol_drop;           /* stop once ||R||_2 <= tol_drop ||R(U0)||_2 (1e-6)    */
+  crn_nk_options nk;
+} crn_steady_options;
+
+typedef struct {
+  double res0, res_final;    /* ||R||_2 of the initial and of the final state        */
+  int32_t steps;             /* updates applied                                     */
+  int32_t krylov_iters;      /* Jacobian-vector products over the solve             */
+  int32_t residual_evals;    /* residual evaluations over the solve                 */
+  int32_t converged;         /* 1 if the drop tol_drop was reached                  */
+} crn_steady_stats;
+
+int crn_nk_options_default(crn_nk_options* o);
+int crn_steady_options_default(crn_steady_options* o);
+
+/* dtau_dev[n_r][n_theta][n_phi] = cfl dt_c from the FP64 state U64_dev
+ * (device).  Asynchronous on `stream`. */
+int crn_local_dt(crn_grid* g, const double* U64_dev, double cfl, double* dtau_dev, void* stream);
+
+/* One Newton-Krylov pseudo-time step at CFL `cfl` on the FP64 master state
+ * U64_dev[9][N] (device, updated in place to U + alpha dU).  The residual runs
+ * in the grid's precision (FP32-bulk grids evaluate it on an FP32 copy).
+ * dU_dev (device, optional) receives dU before alpha; stats (host, optional)
+ * the step's figures.  The first call allocates the workspace ((m + 5) 9N
+ * doubles and 3 x 9N of the grid type).  Synchronises `stream` several times
+ * per Krylov step (the host runs the GMRES recurrences).  Returns
+ * CRN_E_NONPHYSICAL if R(U) flags a cell or no alpha keeps rho, p > 0. */
+int crn_newton_krylov_step(crn_grid* g, double* U64_dev, double cfl, const crn_nk_options* opt,
+                           double* dU_dev, crn_nk_stats* stats, void* stream);
+
+/* Steady solve: Newton-Krylov steps under the CFL law until ||R(U)||_2 <=
+ * tol_drop ||R(U0)||_2 or max_steps updates.  history (host, optional)
+ * receives per pass (cfl, ||R||_2, alpha, krylov_iters), at most history_len
+ * rows of 4 doubles; the last row is the final residual check. */
+int crn_steady_solve(crn_grid* g, double* U64_dev, const crn_steady_options* opt, crn_steady_stats* stats,
+                     double* history, int32_t history_len, void* stream);
+
 /* Synchronise the stream, then read and clear the grid's device error word.
  * Returns CRN_E_NONPHYSICAL if a kernel saw a non-physical state since the
  * last call (crn_last_bad_cell gives the lowest flagged cell index,

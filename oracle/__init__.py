@@ -9,6 +9,11 @@ The arithmetic lives in ``corona_oracle.cpp`` (plain scalar C++ loops, face by
 face, compiled with ``-ffp-contract=off``); this module compiles it with g++
 on first use and marshals numpy arrays through ctypes.
 
+Beyond the residual and its JVP, ``backward_euler_step`` solves the implicit
+pseudo-time step of Sect. 2.1 exactly (dense Jacobian from dual-number JVPs,
+or scipy's GMRES on them), the definition the GPU Newton-Krylov step is
+checked against.
+
 Array layout: conservative state ``U`` of shape ``(9, n0, n1, n2)`` float64,
 variables (rho, rho Vx, rho Vy, rho Vz, Bx, By, Bz, E, psi); for the spherical
 shell the axes are (r, theta, phi), phi fastest.  ``Br`` has shape

@@ -25,7 +25,13 @@
 //   * residual norms, local pseudo-time step bound, explicit pseudo-time
 //     stepping and the res(a) monitor of Sect. 2.1 (log10 of the L2 norm of
 //     a^t - a^{t+1});
-//   * a forward-mode (dual number) Jacobian-vector product of the residual.
+//   * a forward-mode (dual number) Jacobian-vector product of the residual;
+//   * the boundary variants of Sect. 3.2 and 4.1-4.3: the large-E
+//     (Wind-Predict) inner ghost, the low-E ghost with the prescribed V_r*
+//     magnitude, every Table 2 outer law and rho ~ r^-2.5, the mesh with a
+//     thin outermost cell;
+//   * E = -V x B at the inner faces and per cell [Sect. 2.2, 3.1-3.2];
+//   * the local pseudo-time step of the implicit iteration of Sect. 2.1.
 //
 // Readings where the paper is silent are the same as the CUDA library's and
 // are listed in the design notes: Rusanov + GLM-Dedner mixed form without

@@ -54,6 +54,35 @@ class GridDesc(ctypes.Structure):
     ]
 
 
+class NkOptions(ctypes.Structure):
+    _fields_ = [("krylov_dim", ctypes.c_int32), ("max_restarts", ctypes.c_int32),
+                ("lin_rtol", ctypes.c_double), ("fd_rel", ctypes.c_double),
+                ("max_rel_change", ctypes.c_double), ("fd_central", ctypes.c_int32),
+                ("reserved_", ctypes.c_int32)]
+
+
+class NkStats(ctypes.Structure):
+    _fields_ = [("res_l2", ctypes.c_double), ("lin_rel", ctypes.c_double),
+                ("alpha", ctypes.c_double), ("krylov_iters", ctypes.c_int32),
+                ("residual_evals", ctypes.c_int32)]
+
+
+class SteadyOptions(ctypes.Structure):
+    _fields_ = [("cfl0", ctypes.c_double), ("cfl_max", ctypes.c_double),
+                ("cfl_double_every", ctypes.c_int32), ("max_steps", ctypes.c_int32),
+                ("tol_drop", ctypes.c_double), ("nk", NkOptions)]
+
+
+class SteadyStats(ctypes.Structure):
+    _fields_ = [("res0", ctypes.c_double), ("res_final", ctypes.c_double),
+                ("steps", ctypes.c_int32), ("krylov_iters", ctypes.c_int32),
+                ("residual_evals", ctypes.c_int32), ("converged", ctypes.c_int32)]
+
+
+def _struct_dict(st):
+    return {name: getattr(st, name) for name, _ in st._fields_}
+
+
 def library_path() -> str:
     from . import build as _build
     return _build.LIB
@@ -87,6 +116,13 @@ def load_library(build_if_needed: bool = True):
             "crn_last_launch_count": (i32, [vp]),
             "crn_boundary_efield": (ctypes.c_int, [vp, vp, vp, vp]),
             "crn_efield": (ctypes.c_int, [vp, vp, vp, vp]),
+            "crn_nk_options_default": (ctypes.c_int, [ctypes.POINTER(NkOptions)]),
+            "crn_steady_options_default": (ctypes.c_int, [ctypes.POINTER(SteadyOptions)]),
+            "crn_local_dt": (ctypes.c_int, [vp, vp, dbl, vp, vp]),
+            "crn_newton_krylov_step": (ctypes.c_int, [vp, vp, dbl, ctypes.POINTER(NkOptions), vp,
+                                                      ctypes.POINTER(NkStats), vp]),
+            "crn_steady_solve": (ctypes.c_int, [vp, vp, ctypes.POINTER(SteadyOptions),
+                                                ctypes.POINTER(SteadyStats), vp, i32, vp]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(lib, name)
@@ -246,6 +282,65 @@ class Grid:
             E = torch.empty((3,) + self.shape, dtype=torch.float64, device=U.device)
         _check(_lib.crn_efield(self._h, _ptr(U), _ptr(E), _stream_handle(stream)))
         return E
+
+    def local_dt(self, U64, cfl=1.0, out=None, stream=None):
+        """cfl x the local pseudo-time step of every cell, (n_r, n_theta, n_phi) float64."""
+        import torch
+        self._state_check(U64, "U64", torch.float64)
+        if out is None:
+            out = torch.empty(self.shape, dtype=torch.float64, device=U64.device)
+        _check(_lib.crn_local_dt(self._h, _ptr(U64), float(cfl), _ptr(out), _stream_handle(stream)))
+        return out
+
+    @staticmethod
+    def _nk_options(**kw):
+        o = NkOptions()
+        _check(_lib.crn_nk_options_default(ctypes.byref(o)))
+        for k, v in kw.items():
+            if not hasattr(o, k):
+                raise TypeError(f"unknown Newton-Krylov option {k}")
+            setattr(o, k, v)
+        return o
+
+    def newton_krylov_step(self, U64, cfl, dU=None, stream=None, **options):
+        """One backward-Euler pseudo-time step solved by Newton-Krylov
+        (crn_newton_krylov_step); U64 is updated in place.  Returns the step's
+        figures as a dict."""
+        import torch
+        self._state_check(U64, "U64", torch.float64)
+        if dU is not None:
+            self._state_check(dU, "dU", torch.float64)
+        o = self._nk_options(**options)
+        st = NkStats()
+        _check(_lib.crn_newton_krylov_step(self._h, _ptr(U64), float(cfl), ctypes.byref(o), _ptr(dU),
+                                           ctypes.byref(st), _stream_handle(stream)))
+        return _struct_dict(st)
+
+    def steady_solve(self, U64, history_len=None, stream=None, nk=None, **options):
+        """Newton-Krylov steps under the CFL law (crn_steady_solve); U64 is
+        updated in place.  Returns (stats dict, history array of rows
+        (cfl, |R|_2, alpha, krylov_iters))."""
+        import numpy as np
+        import torch
+        self._state_check(U64, "U64", torch.float64)
+        o = SteadyOptions()
+        _check(_lib.crn_steady_options_default(ctypes.byref(o)))
+        for k, v in options.items():
+            if not hasattr(o, k) or k == "nk":
+                raise TypeError(f"unknown steady-solve option {k}")
+            setattr(o, k, v)
+        for k, v in (nk or {}).items():
+            if not hasattr(o.nk, k):
+                raise TypeError(f"unknown Newton-Krylov option {k}")
+            setattr(o.nk, k, v)
+        n = (o.max_steps + 1) if history_len is None else int(history_len)
+        hist = np.zeros((n, 4))
+        st = SteadyStats()
+        _check(_lib.crn_steady_solve(self._h, _ptr(U64), ctypes.byref(o), ctypes.byref(st),
+                                     hist.ctypes.data_as(ctypes.c_void_p), n, _stream_handle(stream)))
+        stats = _struct_dict(st)
+        passes = stats["steps"] + 1
+        return stats, hist[:min(passes, n)]
 
     def sync_status(self, stream=None):
         """Synchronise and raise CoronaError if a kernel flagged a non-physical state."""

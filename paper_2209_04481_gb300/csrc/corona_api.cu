@@ -231,6 +231,7 @@ void free_grid(crn_grid* g) {
   cudaFree(g->rbuf);
   cudaFree(g->shadow);
   cudaFree(g->vjp_buf);
+  crn::nk_free(g->nk);
   delete g;
 }
 

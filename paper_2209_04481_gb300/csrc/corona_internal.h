@@ -11,6 +11,8 @@
 namespace crn {
 
 struct Reduce;
+struct NkWork;                // Newton-Krylov workspace (nk.cu)
+void nk_free(NkWork* w);
 
 // device geometry of one precision (one allocation, carved into arrays)
 template <class T>
@@ -45,6 +47,7 @@ struct crn_grid {
   void* rbuf = nullptr;            // residual scratch for pseudo-time stepping (9N of T)
   void* vjp_buf = nullptr;         // VJP face contributions (allocated by the first VJP call)
   float* shadow = nullptr;         // FP32 shadow of the master state (FP32_BULK)
+  crn::NkWork* nk = nullptr;       // Newton-Krylov workspace (allocated by the first NK call)
   int64_t last_bad_cell = -1;
   int32_t last_launches = 0;
   crn::LaunchCfg cfg;

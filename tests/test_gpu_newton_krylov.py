@@ -1,0 +1,129 @@
+"""The Newton-Krylov pseudo-time iteration (crn_local_dt,
+crn_newton_krylov_step, crn_steady_solve) against the oracle: local time
+steps, one backward-Euler step against the oracle's GMRES solve of the same
+linear system with the exact (dual-number) Jacobian, and steady solves whose
+end state is checked with the oracle's own residual."""
+import numpy as np
+import pytest
+
+import coronal_inputs as ci
+import oracle
+from _util import oracle_grid, problem
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+VR = 1935.07 / ci.V_REF
+BCS = {"low_e": {}, "large_e": dict(inner_bc="large_e", vr_star=VR),
+       "low_e_wp": dict(inner_bc="low_e_wp", vr_star=VR)}
+
+
+def setup(shape, bc, precision="fp64", seed=None):
+    import paper_2209_04481_gb300 as pg
+    U, Br = problem(shape, perturb=seed)
+    if bc == "large_e":
+        Br = ci.potential_field(shape[1], shape[2], dipole_only=shape[1] < 16)
+    g = pg.Grid(*shape, precision=precision, p_b=ci.parker_sound_speed2(), **BCS[bc])
+    g.set_inner_boundary(torch.from_numpy(Br).cuda())
+    return g, U, Br, oracle_grid(shape, **BCS[bc])
+
+
+def per_var_err(a, b):
+    d = np.linalg.norm((a - b).reshape(9, -1), axis=1)
+    s = np.linalg.norm(b.reshape(9, -1), axis=1)
+    return d / (s + 1e-3 * s.max())
+
+
+@pytest.mark.parametrize("precision,rtol", [("fp64", 1e-13), ("fp32", 1e-6)])
+def test_local_dt(precision, rtol):
+    shape = (10, 12, 24)
+    g, U, Br, og = setup(shape, "low_e", precision, seed=3)
+    dt = g.local_dt(torch.from_numpy(U).cuda(), cfl=7.0).cpu().numpy()
+    np.testing.assert_allclose(dt, 7.0 * oracle.local_dt(og, U), rtol=rtol)
+
+
+@pytest.mark.parametrize("bc,cfl,precision,tol", [
+    ("low_e", 2.0, "fp64", 1e-5), ("large_e", 2.0, "fp64", 1e-5), ("low_e_wp", 2.0, "fp64", 1e-5),
+    ("low_e", 20.0, "fp64", 1e-5), ("large_e", 20.0, "fp64", 1e-5), ("low_e_wp", 20.0, "fp64", 1e-5),
+    # FP32-bulk: the central difference of an FP32 residual carries rounding
+    # noise of ~1e-7 of the flux scale over the step, so one step agrees to ~5 %
+    ("large_e", 2.0, "fp32", 0.1), ("low_e_wp", 2.0, "fp32", 0.1)])
+def test_one_step_matches_oracle_solve(bc, cfl, precision, tol):
+    """dU of one step (GMRES to 1e-10 / 1e-5, no limiter) against the oracle's
+    direct solve of (diag(1/(CFL dt)) - J) dU = R with the exact Jacobian
+    (per variable, relative L2)."""
+    shape = (6, 8, 16)
+    g, U, Br, og = setup(shape, bc, precision, seed=5)
+    ref, _ = oracle.backward_euler_step(og, U, Br, cfl, solver="dense")
+    U64 = torch.from_numpy(U).cuda()
+    dU = torch.empty_like(U64)
+    st = g.newton_krylov_step(U64, cfl, dU=dU, krylov_dim=300, max_restarts=4,
+                              lin_rtol=1e-10 if precision == "fp64" else 1e-5, max_rel_change=0.0)
+    g.sync_status()
+    err = per_var_err(dU.cpu().numpy(), ref)
+    assert np.all(err <= tol), (err, st)
+    # one base residual, two per Krylov step (central difference), two per restart
+    assert 2 * st["krylov_iters"] + 1 <= st["residual_evals"] <= 2 * st["krylov_iters"] + 9
+    if st["alpha"] == 1.0:
+        np.testing.assert_allclose(U64.cpu().numpy(), U + dU.cpu().numpy(), rtol=0, atol=0)
+
+
+def test_step_limiter_and_positivity():
+    """alpha = min(1, omega / max relative change of rho and linearised p), and
+    U + alpha dU keeps rho, p > 0."""
+    shape = (8, 8, 16)
+    g, U, Br, og = setup(shape, "low_e", "fp64")
+    U64 = torch.from_numpy(U).cuda()
+    dU = torch.empty_like(U64)
+    st = g.newton_krylov_step(U64, 2.0, dU=dU, max_rel_change=0.3)
+    d = dU.cpu().numpy()
+    W = oracle.cons_to_prim(og, U)
+    rho, V, B, p = W[0], W[1:4], W[4:7], W[7]
+    dp = (og.gamma - 1) * (d[7] - np.sum(V * d[1:4], 0) + 0.5 * np.sum(V * V, 0) * d[0] - np.sum(B * d[4:7], 0))
+    rel = max(np.max(np.abs(d[0]) / rho), np.max(np.abs(dp) / p))
+    alpha = min(1.0, 0.3 / rel)
+    Wn = oracle.cons_to_prim(og, U64.cpu().numpy())
+    assert Wn[0].min() > 0 and Wn[7].min() > 0
+    # the applied step is the limited one, or a power-of-two fraction of it
+    ratio = st["alpha"] / alpha
+    assert ratio <= 1.0 + 1e-12 and abs(np.log2(ratio) - round(np.log2(ratio))) < 1e-9
+
+
+@pytest.mark.parametrize("bc,shape", [("large_e", (16, 8, 16)), ("low_e_wp", (8, 8, 16))])
+def test_steady_solve_reaches_an_oracle_steady_state(bc, shape):
+    """Under the CFL law (2, doubling, 128) the solve drops |R|_2 by 1e-6; the
+    oracle's residual of the final state confirms the drop."""
+    g, U, Br, og = setup(shape, bc, "fp64")
+    U64 = torch.from_numpy(U).cuda()
+    stats, hist = g.steady_solve(U64, max_steps=300, cfl_double_every=10, tol_drop=1e-6)
+    g.sync_status()
+    assert stats["converged"] == 1, (stats, hist[-5:])
+    r0 = np.linalg.norm(oracle.residual(og, U, Br)["R"])
+    r1 = np.linalg.norm(oracle.residual(og, U64.cpu().numpy(), Br)["R"])
+    assert r0 == pytest.approx(stats["res0"], rel=1e-10)
+    assert r1 <= 2e-6 * r0
+    assert hist[0, 0] == 2.0 and hist[:, 0].max() <= 128.0
+
+
+def test_steady_solve_is_deterministic():
+    shape = (8, 8, 16)
+    out = []
+    for _ in range(2):
+        g, U, Br, og = setup(shape, "large_e", "fp64")
+        U64 = torch.from_numpy(U).cuda()
+        g.steady_solve(U64, max_steps=15)
+        out.append(U64.cpu().numpy())
+    assert np.array_equal(out[0], out[1])
+
+
+def test_steady_solve_fp32_bulk():
+    """FP32-bulk residual inside the solve: the drop is limited by FP32
+    rounding of the residual; 1e-4 is reached and confirmed by the oracle."""
+    shape = (16, 8, 16)
+    g, U, Br, og = setup(shape, "large_e", "fp32")
+    U64 = torch.from_numpy(U).cuda()
+    stats, hist = g.steady_solve(U64, max_steps=300, tol_drop=1e-4)
+    assert stats["converged"] == 1, (stats, hist[-5:])
+    r0 = np.linalg.norm(oracle.residual(og, U, Br)["R"])
+    r1 = np.linalg.norm(oracle.residual(og, U64.cpu().numpy(), Br)["R"])
+    assert r1 <= 3e-4 * r0

@@ -53,3 +53,28 @@ def test_null_arguments_are_rejected(lib):
     assert lib.crn_residual(None, None, None, None, None, None) == 1
     assert lib.crn_pseudo_time_step(None, None, 1, 0.4, None, None) == 1
     assert lib.crn_grid_destroy(None) == 0
+
+
+def test_newton_krylov_option_defaults(lib):
+    """The NK option structs round-trip through the library (layout check) with
+    the CFL law of Sect. 4.1 as default: 2, doubling, up to 128."""
+    o = pg.SteadyOptions()
+    assert lib.crn_steady_options_default(ctypes.byref(o)) == 0
+    assert (o.cfl0, o.cfl_max, o.cfl_double_every, o.max_steps, o.tol_drop) == (2.0, 128.0, 10, 500, 1e-6)
+    assert (o.nk.krylov_dim, o.nk.max_restarts, o.nk.lin_rtol, o.nk.fd_rel, o.nk.max_rel_change,
+            o.nk.fd_central) == (30, 0, 1e-3, 0.0, 0.3, 1)
+    n = pg.NkOptions()
+    assert lib.crn_nk_options_default(ctypes.byref(n)) == 0
+    assert n.krylov_dim == 30 and n.lin_rtol == 1e-3
+    assert lib.crn_newton_krylov_step(None, None, 2.0, None, None, None, None) == 1
+    assert lib.crn_steady_solve(None, None, None, None, None, 0, None) == 1
+
+
+@pytest.mark.parametrize("field,value", [("inner_bc", 3), ("r_last", 0.5), ("r_last", 30.0)])
+def test_create_rejects_bad_boundary_fields(lib, field, value):
+    d = pg.GridDesc()
+    lib.crn_grid_desc_default(ctypes.byref(d), 8, 8, 16)
+    setattr(d, field, value)
+    h = ctypes.c_void_p()
+    assert lib.crn_grid_create(ctypes.byref(d), ctypes.byref(h)) == 1
+    assert field in lib.crn_last_error().decode()
