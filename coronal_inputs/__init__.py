@@ -310,3 +310,23 @@ def workload(name):
     else:
         Br = magnetogram(shape[1], shape[2], seed=2209)
     return {"shape": shape, "U": U, "Br": Br, "rho_b": info["rho_b"], "p_b": info["p_b"]}
+
+
+def ensemble_members(n=32, seed=5):
+    """Shapes and magnetogram seeds of the ensemble workload: n shells with
+    N_r ~ U{48..192} and (N_theta, N_phi) drawn uniformly from {24 x 48,
+    48 x 96, 96 x 192} (numpy default_rng(seed), N_r first, then the angular
+    choice); member m takes magnetogram seed m (l <= min(15, N_theta / 2),
+    max |B_r| = 5).  Returns a list of (shape, magnetogram seed)."""
+    rng = np.random.default_rng(seed)
+    nr = rng.integers(48, 193, size=n)
+    ang = rng.integers(0, 3, size=n)
+    choices = [(24, 48), (48, 96), (96, 192)]
+    return [((int(nr[m]),) + choices[int(ang[m])], m) for m in range(n)]
+
+
+def ensemble_member(shape, mseed):
+    """Parker wind + dipole background and the member's magnetogram."""
+    U, info = background(*shape)
+    Br = magnetogram(shape[1], shape[2], seed=mseed, lmax=min(15, shape[1] // 2))
+    return U, Br, info["p_b"]

@@ -284,6 +284,50 @@ int crn_newton_krylov_step(crn_grid* g, double* U64_dev, double cfl, const crn_n
 int crn_steady_solve(crn_grid* g, double* U64_dev, const crn_steady_options* opt, crn_steady_stats* stats,
                      double* history, int32_t history_len, void* stream);
 
+/* ---- ensembles: many shells in one persistent launch ---------------------
+ * An ensemble borrows n grids (one precision and limiter, any sizes; they
+ * must outlive it and must not run their own calls while an ensemble call
+ * on them is in flight).  One persistent launch of the tiled residual takes
+ * work items (member, (theta, phi) tile, radial chunk) from a device counter
+ * until all members are done; every member's R, norms and dtmin are those of
+ * its own crn_residual (bitwise with the same radial chunk).  Arrays of
+ * per-member device pointers are host arrays of n entries. */
+typedef struct crn_ensemble crn_ensemble;
+
+/* CRN_E_ARG if a member is NULL or the members differ in precision, limiter
+ * or device. */
+int crn_ensemble_create(crn_grid* const* grids, int32_t n, crn_ensemble** out);
+int crn_ensemble_destroy(crn_ensemble* e);
+
+/* Radial planes per work item for every member; 0 (default) uses each
+ * member's own choice (the one its crn_residual uses). */
+int crn_ensemble_set_kchunk(crn_ensemble* e, int32_t kchunk);
+int32_t crn_ensemble_kchunk(const crn_ensemble* e);
+
+/* R_dev[m] = R(U_dev[m]) for every member in one launch; norms9_dev
+ * ([n][9]) and dtmin_dev ([n]) are optional device outputs.  Asynchronous. */
+int crn_ensemble_residual(crn_ensemble* e, const void* const* U_dev, void* const* R_dev, double* norms9_dev,
+                          double* dtmin_dev, void* stream);
+
+/* nsteps explicit pseudo-time steps of every member's FP64 master state
+ * U64_dev[m] (as crn_pseudo_time_step, each member with its own dt = cfl x its
+ * dtmin): per step one ensemble residual launch and one batched update
+ * launch.  res_log10_dev ([n][9], optional, device) receives the res(a)
+ * monitor of the last step.  Asynchronous. */
+int crn_ensemble_pseudo_time_step(crn_ensemble* e, double* const* U64_dev, int32_t nsteps, double cfl,
+                                  double* res_log10_dev, void* stream);
+
+/* Tile autotuner: times the ensemble residual (one warm-up, three timed
+ * launches, CUDA events) for the members' own radial chunks and for 4, 6, 8,
+ * 12, 16, 24, 32, 48 planes per item, keeps the fastest (set as with
+ * crn_ensemble_set_kchunk) and returns it in *kchunk_out.  Synchronises
+ * `stream`; R_dev is overwritten. */
+int crn_ensemble_autotune(crn_ensemble* e, const void* const* U_dev, void* const* R_dev, void* stream,
+                          int32_t* kchunk_out);
+
+/* Kernel launches issued by the last call of the ensemble. */
+int32_t crn_ensemble_launch_count(const crn_ensemble* e);
+
 /* Synchronise the stream, then read and clear the grid's device error word.
  * Returns CRN_E_NONPHYSICAL if a kernel saw a non-physical state since the
  * last call (crn_last_bad_cell gives the lowest flagged cell index,

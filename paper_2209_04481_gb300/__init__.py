@@ -123,6 +123,14 @@ def load_library(build_if_needed: bool = True):
                                                       ctypes.POINTER(NkStats), vp]),
             "crn_steady_solve": (ctypes.c_int, [vp, vp, ctypes.POINTER(SteadyOptions),
                                                 ctypes.POINTER(SteadyStats), vp, i32, vp]),
+            "crn_ensemble_create": (ctypes.c_int, [vp, i32, ctypes.POINTER(vp)]),
+            "crn_ensemble_destroy": (ctypes.c_int, [vp]),
+            "crn_ensemble_set_kchunk": (ctypes.c_int, [vp, i32]),
+            "crn_ensemble_kchunk": (i32, [vp]),
+            "crn_ensemble_launch_count": (i32, [vp]),
+            "crn_ensemble_residual": (ctypes.c_int, [vp, vp, vp, vp, vp, vp]),
+            "crn_ensemble_pseudo_time_step": (ctypes.c_int, [vp, vp, i32, dbl, vp, vp]),
+            "crn_ensemble_autotune": (ctypes.c_int, [vp, vp, vp, vp, ctypes.POINTER(i32)]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(lib, name)
@@ -416,3 +424,80 @@ def __getattr__(name):
             _Lazy.fn = _make_residual_function()
         return _Lazy.fn
     raise AttributeError(name)
+
+
+def _ptr_array(tensors):
+    arr = (ctypes.c_void_p * len(tensors))(*[t.data_ptr() for t in tensors])
+    return arr
+
+
+class Ensemble:
+    """Many grids (one precision and limiter, any sizes) evaluated by one
+    persistent launch (``crn_ensemble_*``).  The grids must outlive the
+    ensemble; per-member tensors are passed as lists in member order."""
+
+    def __init__(self, grids):
+        lib = load_library()
+        self.grids = list(grids)
+        hs = (ctypes.c_void_p * len(self.grids))(*[g._h.value for g in self.grids])
+        h = ctypes.c_void_p()
+        _check(lib.crn_ensemble_create(hs, len(self.grids), ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.crn_ensemble_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def kchunk(self):
+        return int(_lib.crn_ensemble_kchunk(self._h))
+
+    @kchunk.setter
+    def kchunk(self, k):
+        _check(_lib.crn_ensemble_set_kchunk(self._h, int(k)))
+
+    @property
+    def last_launch_count(self):
+        return int(_lib.crn_ensemble_launch_count(self._h))
+
+    def _check_states(self, Us, name, dtype=None):
+        if len(Us) != len(self.grids):
+            raise ValueError(f"{name}: one tensor per member")
+        for g, U in zip(self.grids, Us):
+            g._state_check(U, name, dtype)
+
+    def residual(self, Us, Rs=None, norms=None, dtmin=None, stream=None):
+        """Rs[m] = R(Us[m]) for all members in one launch; optional norms
+        (n, 9) and dtmin (n,) float64 device tensors."""
+        import torch
+        self._check_states(Us, "U")
+        if Rs is None:
+            Rs = [torch.empty_like(U) for U in Us]
+        self._check_states(Rs, "R")
+        _check(_lib.crn_ensemble_residual(self._h, _ptr_array(Us), _ptr_array(Rs), _ptr(norms), _ptr(dtmin),
+                                          _stream_handle(stream)))
+        return Rs
+
+    def pseudo_time_step(self, U64s, nsteps, cfl, res_log10=None, stream=None):
+        """nsteps explicit steps of every member's FP64 master state (in place)."""
+        import torch
+        self._check_states(U64s, "U64", torch.float64)
+        _check(_lib.crn_ensemble_pseudo_time_step(self._h, _ptr_array(U64s), int(nsteps), float(cfl),
+                                                  _ptr(res_log10), _stream_handle(stream)))
+        return U64s
+
+    def autotune(self, Us, Rs, stream=None):
+        """Time the candidate radial chunks and keep the fastest; returns it."""
+        self._check_states(Us, "U")
+        self._check_states(Rs, "R")
+        k = ctypes.c_int32()
+        _check(_lib.crn_ensemble_autotune(self._h, _ptr_array(Us), _ptr_array(Rs), _stream_handle(stream),
+                                          ctypes.byref(k)))
+        return int(k.value)

@@ -68,6 +68,22 @@ cudaError_t launch_vjp_fp64(crn_grid* g, const double* U, const double* Rb, doub
 cudaError_t launch_vjp_fp32(crn_grid* g, const float* U, const float* Rb, float* Ub, double* Brb,
                             cudaStream_t st, int* nlaunch);
 size_t vjp_scratch_bytes(const crn_grid* g);
+// ensemble records (EnsMember<T> of residual.cuh, opaque here) and launches
+size_t ens_member_bytes_fp64();
+size_t ens_member_bytes_fp32();
+int ens_fill_fp64(crn_grid* g, const void* U, void* R, int kchunk, int item0, double* nu, double* du, void* dst);
+int ens_fill_fp32(crn_grid* g, const void* U, void* R, int kchunk, int item0, double* nu, double* du, void* dst);
+cudaError_t launch_ensemble_fp64(const void* dev, int nmem, int nitems, unsigned int* next, int limiter,
+                                 int nctas, cudaStream_t st);
+cudaError_t launch_ensemble_fp32(const void* dev, int nmem, int nitems, unsigned int* next, int limiter,
+                                 int nctas, cudaStream_t st);
+int ensemble_ctas_per_sm_fp64(int limiter);
+int ensemble_ctas_per_sm_fp32(int limiter);
+cudaError_t launch_ensemble_update(const void* dev, int nmem, int nitems, double cfl, bool fp32,
+                                   cudaStream_t st);
+size_t ens_update_bytes();
+unsigned update_blocks(const crn_grid* g);
+void ens_update_fill(crn_grid* g, double* U64, int item0, int nitems, double* log_out, void* dst);
 cudaError_t launch_efield_fp64(crn_grid* g, const double* U, double* E, bool volume, cudaStream_t st,
                                 int* nl);
 cudaError_t launch_efield_fp32(crn_grid* g, const float* U, double* E, bool volume, cudaStream_t st,

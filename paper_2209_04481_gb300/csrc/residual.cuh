@@ -73,8 +73,9 @@ __device__ __forceinline__ void flag_bad(const Reduce& red, long long cell) {
 // WARP_DONE: the caller has already reduced within each warp (lane 0 holds
 // the warp's sums, every lane the warp's minimum).
 template <int NTHREADS, bool WARP_DONE = false>
-__device__ void reduce_and_finalize(const double (&sum)[NV], double dtmin, const Reduce& red,
-                                    double* scratch /* >= (NTHREADS/32) * RED_STRIDE doubles */) {
+__device__ void reduce_and_finalize_at(const double (&sum)[NV], double dtmin, const Reduce& red,
+                                       double* scratch /* >= (NTHREADS/32) * RED_STRIDE doubles */,
+                                       int bid, int nblocks) {
   constexpr int NW = NTHREADS / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double v[NV + 1];
@@ -95,8 +96,6 @@ __device__ void reduce_and_finalize(const double (&sum)[NV], double dtmin, const
     for (int q = 0; q <= NV; ++q) scratch[warp * RED_STRIDE + q] = v[q];
   }
   __syncthreads();
-  const int nblocks = gridDim.x * gridDim.y;
-  const int bid = blockIdx.y * gridDim.x + blockIdx.x;
   if (threadIdx.x <= NV) {
     const int q = threadIdx.x;
     double a = scratch[q];
@@ -151,6 +150,14 @@ __device__ void reduce_and_finalize(const double (&sum)[NV], double dtmin, const
     }
   }
   if (threadIdx.x == 0) *red.counter = 0u;
+}
+
+// the same with the block id and count of the launch grid
+template <int NTHREADS, bool WARP_DONE = false>
+__device__ __forceinline__ void reduce_and_finalize(const double (&sum)[NV], double dtmin, const Reduce& red,
+                                                    double* scratch) {
+  reduce_and_finalize_at<NTHREADS, WARP_DONE>(sum, dtmin, red, scratch, blockIdx.y * gridDim.x + blockIdx.x,
+                                              gridDim.x * gridDim.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -412,15 +419,18 @@ __device__ __forceinline__ void load_raw(const T* __restrict__ src, int64_t N, i
 // (16 warps); FP64 CTAs are limited to one by their shared memory anyway
 template <class T> struct MinCtas { static constexpr int value = sizeof(T) == 4 ? 2 : 1; };
 
+// One work item of the tiled residual: tile `tile` (row-major over the
+// (theta, phi) tiles) and radial chunk `chunk` of one grid; `bid` / `nblocks`
+// number the items of that grid for its cross-CTA reduction.
 template <class T, int LIM, int TT, int TP>
-__global__ void __launch_bounds__(TT * TP, MinCtas<T>::value)
-residual_tiled(Shape sh, Geo<T> g, Phys<T> ph, const double* __restrict__ Br,
-               const T* __restrict__ U, T* __restrict__ R, Reduce red, int kchunk) {
+__device__ __forceinline__ void tiled_item(const Shape& sh, const Geo<T>& g, const Phys<T>& ph,
+                                           const double* __restrict__ Br, const T* __restrict__ U,
+                                           T* __restrict__ R, const Reduce& red, int kchunk, int tile,
+                                           int chunk, int bid, int nblocks, unsigned char* smem_raw) {
   using D = TileDims<TT, TP>;
   constexpr int NT = D::NT, HP = D::HP, HC = D::HC, NTV = D::NTV, NPV = D::NPV, NF = D::NF;
   static_assert(D::NHALO <= NT, "each thread stores at most one halo position");
   static_assert(D::NEXTRA_F <= NT && NT % 32 == 0, "tile shape");
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   T* ring = reinterpret_cast<T*>(smem_raw);  // [3][NV][HC]   primitives of planes k..k+2
   T* tvu = ring + 3 * NV * HC;               // [NV][NTV]     theta: upper value of the row below face f
   T* tvl = tvu + NV * NTV;                   // [NV][NTV]     theta: lower value of the row above face f
@@ -446,8 +456,8 @@ residual_tiled(Shape sh, Geo<T> g, Phys<T> ph, const double* __restrict__ Br,
   const int64_t N = sh.ncell, cs = (int64_t)nt * np;
   const int tid = threadIdx.x;
   const int ntp = (np + TP - 1) / TP;
-  const int j0 = (blockIdx.x / ntp) * TT, i0 = (blockIdx.x % ntp) * TP;
-  const int k0 = blockIdx.y * kchunk;
+  const int j0 = (tile / ntp) * TT, i0 = (tile % ntp) * TP;
+  const int k0 = chunk * kchunk;
   const int k1 = min(nr, k0 + kchunk);
   const int jj = tid / TP, ii = tid % TP;
   const int jo = j0 + jj, io = i0 + ii;
@@ -790,7 +800,57 @@ residual_tiled(Shape sh, Geo<T> g, Phys<T> ph, const double* __restrict__ Br,
 #pragma unroll
   for (int v = 0; v < NV; ++v) tot[v] = (threadIdx.x & 31) == 0 ? (double)sq[v] : 0.0;
   double* scratch = reinterpret_cast<double*>(smem_raw);
-  reduce_and_finalize<NT, true>(tot, (double)dtm, red, scratch);
+  reduce_and_finalize_at<NT, true>(tot, (double)dtm, red, scratch, bid, nblocks);
+}
+
+// one grid: block (x, y) = (tile, radial chunk)
+template <class T, int LIM, int TT, int TP>
+__global__ void __launch_bounds__(TT * TP, MinCtas<T>::value)
+residual_tiled(Shape sh, Geo<T> g, Phys<T> ph, const double* __restrict__ Br,
+               const T* __restrict__ U, T* __restrict__ R, Reduce red, int kchunk) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  tiled_item<T, LIM, TT, TP>(sh, g, ph, Br, U, R, red, kchunk, blockIdx.x, blockIdx.y,
+                             blockIdx.y * gridDim.x + blockIdx.x, gridDim.x * gridDim.y, smem_raw);
+}
+
+// ---------------------------------------------------------------------------
+// ensemble: many grids (same precision and limiter, any sizes) in one
+// persistent launch.  Work items are (member, tile, radial chunk), numbered
+// member by member; CTAs take items from a global counter (zeroed before the
+// launch) until none are left.  Each member keeps its own reduction scratch,
+// so its norms and dtmin come out exactly as from its own launch with the
+// same radial chunk.
+// ---------------------------------------------------------------------------
+template <class T>
+struct EnsMember {
+  Shape sh;
+  Geo<T> g;
+  Phys<T> ph;
+  const double* Br;
+  const T* U;
+  T* R;
+  Reduce red;
+  int kchunk, ntiles, nitems, item0;
+};
+
+template <class T, int LIM, int TT, int TP>
+__global__ void __launch_bounds__(TT * TP, MinCtas<T>::value)
+residual_ensemble(const EnsMember<T>* __restrict__ mem, int nmem, int nitems, unsigned int* __restrict__ next) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_item;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(next, 1u);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= nitems) break;
+    int m = 0;
+    while (m + 1 < nmem && mem[m + 1].item0 <= item) ++m;
+    const EnsMember<T>& M = mem[m];
+    const int local = item - M.item0;
+    tiled_item<T, LIM, TT, TP>(M.sh, M.g, M.ph, M.Br, M.U, M.R, M.red, M.kchunk, local % M.ntiles,
+                               local / M.ntiles, local, M.nitems, smem_raw);
+    __syncthreads();  // shared memory and s_item are reused by the next item
+  }
 }
 
 }  // namespace crn

@@ -109,6 +109,56 @@ cudaError_t efield_t(crn_grid* g, const T* U, double* E, bool volume, cudaStream
   return cudaGetLastError();
 }
 
+// ---- ensemble: member records and the persistent launch
+template <class T>
+void ens_fill_t(crn_grid* g, const T* U, T* R, int kchunk, int item0, double* norms_user, double* dt_user,
+                EnsMember<T>* m) {
+  constexpr int TT = TileFor<T>::TT, TP = TileFor<T>::TP;
+  m->sh = g->shape;
+  m->g = geo_of<T>(g);
+  m->ph = phys_of<T>(g);
+  m->Br = g->br;
+  m->U = U;
+  m->R = R;
+  m->red = make_reduce(g, norms_user, dt_user);
+  m->kchunk = kchunk;
+  m->ntiles = ((g->shape.nt + TT - 1) / TT) * ((g->shape.np + TP - 1) / TP);
+  m->nitems = m->ntiles * ((g->shape.nr + kchunk - 1) / kchunk);
+  m->item0 = item0;
+}
+
+template <class T>
+cudaError_t launch_ensemble_t(const EnsMember<T>* dev, int nmem, int nitems, unsigned int* next, int limiter,
+                              int nctas, cudaStream_t st) {
+  constexpr int TT = TileFor<T>::TT, TP = TileFor<T>::TP;
+  const size_t smem = TileDims<TT, TP>::template smem_bytes<T>();
+  cudaError_t e = cudaMemsetAsync(next, 0, sizeof(unsigned int), st);
+  if (e != cudaSuccess) return e;
+  if (limiter == CRN_LIM_NONE)
+    residual_ensemble<T, 0, TT, TP><<<nctas, TT * TP, smem, st>>>(dev, nmem, nitems, next);
+  else if (limiter == CRN_LIM_MINMOD)
+    residual_ensemble<T, 1, TT, TP><<<nctas, TT * TP, smem, st>>>(dev, nmem, nitems, next);
+  else
+    residual_ensemble<T, 2, TT, TP><<<nctas, TT * TP, smem, st>>>(dev, nmem, nitems, next);
+  return cudaGetLastError();
+}
+
+// shared-memory opt-in and resident CTAs per SM of the ensemble kernel
+template <class T>
+int ensemble_ctas_t(int limiter) {
+  constexpr int TT = TileFor<T>::TT, TP = TileFor<T>::TP;
+  const int smem = (int)TileDims<TT, TP>::template smem_bytes<T>();
+  auto setup = [&](auto kern) {
+    int n = 0;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, TT * TP, smem) != cudaSuccess) return 0;
+    return n;
+  };
+  if (limiter == CRN_LIM_NONE) return setup(residual_ensemble<T, 0, TT, TP>);
+  if (limiter == CRN_LIM_MINMOD) return setup(residual_ensemble<T, 1, TT, TP>);
+  return setup(residual_ensemble<T, 2, TT, TP>);
+}
+
 template <class T>
 size_t tiled_smem_t() {
   using D = TileDims<TileFor<T>::TT, TileFor<T>::TP>;

@@ -38,18 +38,17 @@ __device__ __forceinline__ void monitor_increments(const TM (&u0)[NV], const TM 
 
 // TR: element type of R (double on FP64 grids, float on FP32_BULK grids);
 // the monitor arithmetic runs in the same type.
+// block `bid` of `nblocks` blocks covering the N cells of one grid
 template <class TR>
-__global__ void __launch_bounds__(256)
-update_kernel(int64_t N, double* __restrict__ U, const TR* __restrict__ R,
-              const float* shadow_old, float* shadow_new,
-              const double* __restrict__ dtmin, double cfl, TR gm1, Reduce red) {
-  __shared__ double scratch[8 * RED_STRIDE];
+__device__ __forceinline__ void update_block(int64_t N, double* __restrict__ U, const TR* __restrict__ R,
+                                             const float* shadow_old, float* shadow_new,
+                                             const double* __restrict__ dtmin, double cfl, TR gm1,
+                                             const Reduce& red, int bid, int nblocks, double* scratch) {
   const double dt = cfl * dtmin[0];
   const TR dtr = (TR)dt;
   Acc<TR> acc;
   acc.init();
-  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < N;
-       c += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t c = (int64_t)bid * blockDim.x + threadIdx.x; c < N; c += (int64_t)nblocks * blockDim.x) {
     TR u0[NV], du[NV], dw[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
@@ -69,7 +68,74 @@ update_kernel(int64_t N, double* __restrict__ U, const TR* __restrict__ R,
   double tot[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) tot[v] = acc.total(v);
-  reduce_and_finalize<256>(tot, INFINITY, red, scratch);
+  reduce_and_finalize_at<256>(tot, INFINITY, red, scratch, bid, nblocks);
+}
+
+template <class TR>
+__global__ void __launch_bounds__(256)
+update_kernel(int64_t N, double* __restrict__ U, const TR* __restrict__ R,
+              const float* shadow_old, float* shadow_new,
+              const double* __restrict__ dtmin, double cfl, TR gm1, Reduce red) {
+  __shared__ double scratch[8 * RED_STRIDE];
+  update_block<TR>(N, U, R, shadow_old, shadow_new, dtmin, cfl, gm1, red, blockIdx.x, gridDim.x, scratch);
+}
+
+// ensemble: one block per (member, block) item, members numbered in order
+struct EnsUpdate {
+  int64_t N;
+  double* U;
+  const void* R;       // the member's residual buffer (FP32 or FP64)
+  float* shadow;       // FP32 shadow (FP32-bulk members), else null
+  const double* dtmin;
+  double gm1;
+  Reduce red;
+  int item0, nitems;
+};
+
+template <class TR>
+__global__ void __launch_bounds__(256)
+ensemble_update_kernel(const EnsUpdate* __restrict__ mem, int nmem, double cfl) {
+  __shared__ double scratch[8 * RED_STRIDE];
+  const int item = blockIdx.x;
+  int m = 0;
+  while (m + 1 < nmem && mem[m + 1].item0 <= item) ++m;
+  const EnsUpdate& M = mem[m];
+  update_block<TR>(M.N, M.U, static_cast<const TR*>(M.R), M.shadow, M.shadow, M.dtmin, cfl, (TR)M.gm1,
+                   M.red, item - M.item0, M.nitems, scratch);
+}
+
+size_t ens_update_bytes() { return sizeof(EnsUpdate); }
+
+void ens_update_fill(crn_grid* g, double* U64, int item0, int nitems, double* log_out, void* dst) {
+  EnsUpdate* m = static_cast<EnsUpdate*>(dst);
+  m->N = g->shape.ncell;
+  m->U = U64;
+  m->R = g->rbuf;
+  m->shadow = g->d.precision == CRN_FP64 ? nullptr : g->shadow;
+  m->dtmin = g->stats + 9;
+  m->gm1 = g->d.gamma - 1.0;
+  Reduce& red = m->red;
+  red.partials = g->partials;
+  red.counter = g->counter;
+  red.norms_out = nullptr;
+  red.dt_out = nullptr;
+  red.norms_user = nullptr;
+  red.dt_user = nullptr;
+  red.err_flags = g->err_flags;
+  red.err_cell = g->err_cell;
+  red.log_out = log_out ? log_out : g->stats + 10;
+  m->item0 = item0;
+  m->nitems = nitems;
+}
+
+cudaError_t launch_ensemble_update(const void* dev, int nmem, int nitems, double cfl, bool fp32,
+                                   cudaStream_t st) {
+  const EnsUpdate* m = static_cast<const EnsUpdate*>(dev);
+  if (fp32)
+    ensemble_update_kernel<float><<<nitems, 256, 0, st>>>(m, nmem, cfl);
+  else
+    ensemble_update_kernel<double><<<nitems, 256, 0, st>>>(m, nmem, cfl);
+  return cudaGetLastError();
 }
 
 __global__ void __launch_bounds__(256)
@@ -79,7 +145,7 @@ shadow_kernel(int64_t n, const double* __restrict__ U, float* __restrict__ S) {
     S[q] = (float)U[q];
 }
 
-static unsigned update_blocks(const crn_grid* g) {
+unsigned update_blocks(const crn_grid* g) {
   int64_t nb = (g->shape.ncell + 255) / 256;
   if (nb > (int64_t)g->max_blocks) nb = (int64_t)g->max_blocks;
   if (nb > 4 * 152 * 8) nb = 4 * 152 * 8;

@@ -78,3 +78,11 @@ def test_create_rejects_bad_boundary_fields(lib, field, value):
     h = ctypes.c_void_p()
     assert lib.crn_grid_create(ctypes.byref(d), ctypes.byref(h)) == 1
     assert field in lib.crn_last_error().decode()
+
+
+def test_ensemble_arguments_checked_on_the_host(lib):
+    h = ctypes.c_void_p()
+    assert lib.crn_ensemble_create(None, 0, ctypes.byref(h)) == 1
+    assert lib.crn_ensemble_residual(None, None, None, None, None, None) == 1
+    assert lib.crn_ensemble_set_kchunk(None, 4) == 1
+    assert lib.crn_ensemble_destroy(None) == 0
