@@ -98,6 +98,8 @@ typedef struct {
                                    in (r_in, r_out): n_r - 1 geometric cells up to r_last
                                    and one thin last cell [r_last, r_out], the mesh with a
                                    small outer ghost of Sect. 4.3 (not for crn_residual_static) */
+  double psi_damp;              /* GLM damping rate alpha >= 0: source -alpha psi in the psi
+                                   equation (0, the default: the undamped cleaning of Sect. 2.1) */
 } crn_grid_desc;
 
 typedef struct crn_grid crn_grid;
@@ -191,6 +193,17 @@ int crn_pseudo_time_step(crn_grid* g, double* U64_dev, int32_t nsteps, double cf
  * cudaFree or other allocating routine.  Asynchronous on `stream`. */
 int crn_residual_static(const crn_grid_desc* d, const double* Br_dev, const void* U_dev,
                         void* R_dev, double* norms9_dev, double* dtmin_dev, void* stream);
+
+/* Residuals of `count` independent states in HOST memory: R_host[i] =
+ * R(U_host[i]) (layout as crn_residual, the grid's precision), optional
+ * norms9_host[i][9] and dtmin_host[i].  The copies run on two internal
+ * streams around the residual launches on `stream`, through two device
+ * staging slots owned by the grid (allocated by the first call), so that the
+ * copy of state i + 1 in, the residual of state i and the copy of R_{i-1} out
+ * overlap; page-locked (pinned) host buffers are needed for the copies to
+ * overlap.  Synchronous: returns when every result is in host memory. */
+int crn_residual_host_batch(crn_grid* g, const void* const* U_host, void* const* R_host, double* norms9_host,
+                            double* dtmin_host, int32_t count, void* stream);
 
 /* Boundary electric field diagnostic [Sect. 2.2: E = -V x B; Sect. 3.2
  * compares the inner-boundary E of the low-E and large-E formulations]:
@@ -327,6 +340,18 @@ int crn_ensemble_autotune(crn_ensemble* e, const void* const* U_dev, void* const
 
 /* Kernel launches issued by the last call of the ensemble. */
 int32_t crn_ensemble_launch_count(const crn_ensemble* e);
+
+/* Sensitivity of a functional g(U) of a steady state U* (R(U*, B_b) = 0) to
+ * the prescribed inner field B_b (B_r, or (B_r, B_theta) for large-E):
+ * solves J^T lambda = gbar (J = dR/dU at U64_dev, gbar = dg/dU, FP64 [9][N],
+ * device) by GMRES on J^T diag(dt_c) with the hand-written VJP of
+ * crn_residual_vjp, and writes sens_dev = dg/dB_b = -(dR/dB_b)^T lambda
+ * (FP64, the shape crn_set_inner_boundary takes) and, if lambda_dev is not
+ * NULL, lambda.  opt: krylov_dim, max_restarts and lin_rtol are used.  The
+ * first call allocates the Newton-Krylov and VJP workspaces.  Synchronises
+ * `stream` once or twice per Krylov step. */
+int crn_adjoint_solve(crn_grid* g, const double* U64_dev, const double* gbar_dev, double* lambda_dev,
+                      double* sens_dev, const crn_nk_options* opt, crn_nk_stats* stats, void* stream);
 
 /* Synchronise the stream, then read and clear the grid's device error word.
  * Returns CRN_E_NONPHYSICAL if a kernel saw a non-physical state since the

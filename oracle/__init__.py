@@ -71,6 +71,7 @@ class _Desc(ctypes.Structure):
         ("outer_psi_extrap", ctypes.c_int32), ("pad_", ctypes.c_int32),
         ("vr_star", ctypes.c_double), ("outer_bphi_exp", ctypes.c_double),
         ("outer_vphi_exp", ctypes.c_double), ("r_last", ctypes.c_double),
+        ("psi_damp", ctypes.c_double),
     ]
 
 
@@ -130,6 +131,7 @@ class Grid:
     outer_vr_mass: bool = False
     outer_psi_extrap: bool = False
     r_last: float = 0.0              # > 0: thin last cell [r_last, r_out] (Sect. 4.3)
+    psi_damp: float = 0.0            # GLM damping rate alpha (source -alpha psi)
     geom: int = GEOM_SPHERE
     lengths: tuple = (1.0, 1.0, 1.0)
     bcs: tuple = (BC_PERIODIC, BC_PERIODIC, BC_PERIODIC)
@@ -161,6 +163,7 @@ class Grid:
         d.vr_star = self.vr_star
         d.outer_bphi_exp, d.outer_vphi_exp = self.outer_bphi_exp, self.outer_vphi_exp
         d.r_last = self.r_last
+        d.psi_damp = self.psi_damp
         return d
 
     @property
@@ -355,6 +358,23 @@ def backward_euler_step(grid: Grid, U, Br, cfl, solver="dense", rtol=1e-12, J=No
         if info != 0:
             raise RuntimeError(f"GMRES did not reach rtol {rtol} (info {info})")
     return dU.reshape(U.shape), R
+
+
+def steady_sensitivity(grid: Grid, U, Br, gbar, dBr, rtol=1e-12):
+    """Directional sensitivity of g at a steady state R(U*, B) = 0 by the
+    implicit function theorem: dg = -gbar . J^-1 (dR/dB . dBr), J = dR/dU at
+    U (dual-number JVPs; scipy GMRES on J to rtol)."""
+    from scipy.sparse.linalg import LinearOperator, gmres
+    U = _f64(U, (9,) + grid.shape)
+    zero_b = np.zeros(np.shape(Br))
+    v = residual_jvp(grid, U, Br, np.zeros_like(U), dBr)[1].ravel()
+    n = U.size
+    A = LinearOperator((n, n), matvec=lambda x: residual_jvp(grid, U, Br, x.reshape(U.shape), zero_b)[1].ravel(),
+                       dtype=np.float64)
+    w, info = gmres(A, v, rtol=rtol, atol=0.0, restart=300, maxiter=100)
+    if info != 0:
+        raise RuntimeError(f"GMRES did not reach rtol {rtol} (info {info})")
+    return -float(np.dot(np.ravel(gbar), w))
 
 
 def efield(grid: Grid, U):

@@ -120,6 +120,7 @@ typedef struct {
   double outer_bphi_exp;   // outer ghost: B_phi scaled by (r_I/r_G)^c
   double outer_vphi_exp;   // outer ghost: V_phi scaled by (r_I/r_G)^e
   double r_last;           // 0: geometric faces; else the last cell is [r_last, r_out] (Sect. 4.3)
+  double psi_damp;         // GLM damping rate alpha: source -alpha psi (0: undamped, Sect. 2.1)
 } orc_desc;
 }
 
@@ -616,6 +617,8 @@ void residual_core(const Mesh& m, const T* U, const T* Br, Residual<T>& res) {
           res.R[U_MZ * N + id] += rho * g[2];
           res.R[U_E * N + id] += mg;
         }
+        // GLM damping of the cleaning scalar: d psi/dt += -alpha psi
+        res.R[U_PSI * N + id] -= m.d.psi_damp * U[U_PSI * N + id];
       }
 }
 
@@ -630,6 +633,7 @@ bool desc_ok(const orc_desc* d) {
   } else if (d->geom != GEOM_BOX) {
     return false;
   }
+  if (!(d->psi_damp >= 0.0)) return false;
   return d->gamma > 1.0;
 }
 

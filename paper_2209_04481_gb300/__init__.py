@@ -51,6 +51,7 @@ class GridDesc(ctypes.Structure):
         ("outer_psi_extrap", ctypes.c_int32), ("reserved_", ctypes.c_int32),
         ("vr_star", ctypes.c_double), ("outer_bphi_exp", ctypes.c_double),
         ("outer_vphi_exp", ctypes.c_double), ("r_last", ctypes.c_double),
+        ("psi_damp", ctypes.c_double),
     ]
 
 
@@ -123,6 +124,9 @@ def load_library(build_if_needed: bool = True):
                                                       ctypes.POINTER(NkStats), vp]),
             "crn_steady_solve": (ctypes.c_int, [vp, vp, ctypes.POINTER(SteadyOptions),
                                                 ctypes.POINTER(SteadyStats), vp, i32, vp]),
+            "crn_residual_host_batch": (ctypes.c_int, [vp, vp, vp, vp, vp, i32, vp]),
+            "crn_adjoint_solve": (ctypes.c_int, [vp, vp, vp, vp, vp, ctypes.POINTER(NkOptions),
+                                                 ctypes.POINTER(NkStats), vp]),
             "crn_ensemble_create": (ctypes.c_int, [vp, i32, ctypes.POINTER(vp)]),
             "crn_ensemble_destroy": (ctypes.c_int, [vp]),
             "crn_ensemble_set_kchunk": (ctypes.c_int, [vp, i32]),
@@ -324,6 +328,21 @@ class Grid:
                                            ctypes.byref(st), _stream_handle(stream)))
         return _struct_dict(st)
 
+    def adjoint_solve(self, U64, gbar, lam=None, stream=None, **options):
+        """dg/dB_b at the steady state U64 for dg/dU = gbar (crn_adjoint_solve):
+        returns (sensitivity of the boundary shape, lambda or None, stats dict)."""
+        import torch
+        self._state_check(U64, "U64", torch.float64)
+        self._state_check(gbar, "gbar", torch.float64)
+        if lam is not None:
+            self._state_check(lam, "lambda", torch.float64)
+        sens = torch.empty(self.boundary_shape, dtype=torch.float64, device=U64.device)
+        o = self._nk_options(**options)
+        st = NkStats()
+        _check(_lib.crn_adjoint_solve(self._h, _ptr(U64), _ptr(gbar), _ptr(lam), _ptr(sens), ctypes.byref(o),
+                                      ctypes.byref(st), _stream_handle(stream)))
+        return sens, lam, _struct_dict(st)
+
     def steady_solve(self, U64, history_len=None, stream=None, nk=None, **options):
         """Newton-Krylov steps under the CFL law (crn_steady_solve); U64 is
         updated in place.  Returns (stats dict, history array of rows
@@ -357,6 +376,23 @@ class Grid:
     @property
     def last_bad_cell(self):
         return int(_lib.crn_last_bad_cell(self._h))
+
+    def residual_host_batch(self, U_hosts, R_hosts, norms=None, dtmin=None, stream=None):
+        """R_hosts[i] = R(U_hosts[i]) for CPU tensors (pinned for overlap) through
+        crn_residual_host_batch: copies in/out overlapped with the residuals.
+        norms (count, 9) and dtmin (count,) are optional float64 CPU tensors."""
+        import torch
+        if len(U_hosts) != len(R_hosts):
+            raise ValueError("one R buffer per state")
+        for t in list(U_hosts) + list(R_hosts):
+            if t.is_cuda or t.dtype != self.dtype or not t.is_contiguous() or t.numel() != 9 * self.ncell:
+                raise ValueError(f"host buffers must be contiguous {self.dtype} CPU tensors of 9 x {self.shape}")
+        for t in (norms, dtmin):
+            if t is not None and (t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous()):
+                raise ValueError("norms / dtmin must be contiguous float64 CPU tensors")
+        _check(_lib.crn_residual_host_batch(self._h, _ptr_array(U_hosts), _ptr_array(R_hosts), _ptr(norms),
+                                            _ptr(dtmin), len(U_hosts), _stream_handle(stream)))
+        return R_hosts
 
     def residual_host(self, U_host, R_host, norms=None, dtmin=None, stream=None):
         """End-to-end call on host (pinned) buffers: copy U in, evaluate, copy R out.

@@ -71,6 +71,7 @@ int validate(const crn_grid_desc* d) {
     return fail(CRN_E_ARG, "vr_star and the outer exponents must be finite");
   if (d->r_last != 0.0 && !(finite(d->r_last) && d->r_last > d->r_in && d->r_last < d->r_out))
     return fail(CRN_E_ARG, "r_last must be 0 or in (r_in, r_out)");
+  if (!(finite(d->psi_damp) && d->psi_damp >= 0.0)) return fail(CRN_E_ARG, "psi_damp must be >= 0");
   return CRN_OK;
 }
 
@@ -213,6 +214,7 @@ crn::Phys<T> make_phys(const crn_grid_desc& d, const HostGeo& h) {
   ph.fvr = (T)h.fvr;
   ph.fvp = (T)h.fvp;
   ph.psi_out = d.outer_psi_extrap ? (T)1 : (T)-1;
+  ph.psi_damp = (T)d.psi_damp;
   ph.inner_bc = d.inner_bc;
   ph.vr_star = d.vr_star;
   return ph;
@@ -232,6 +234,7 @@ void free_grid(crn_grid* g) {
   cudaFree(g->shadow);
   cudaFree(g->vjp_buf);
   crn::nk_free(g->nk);
+  crn::host_pipe_free(g->pipe);
   delete g;
 }
 

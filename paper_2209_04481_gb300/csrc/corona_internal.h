@@ -13,6 +13,8 @@ namespace crn {
 struct Reduce;
 struct NkWork;                // Newton-Krylov workspace (nk.cu)
 void nk_free(NkWork* w);
+struct HostPipe;              // host-buffer staging (host_io.cu)
+void host_pipe_free(HostPipe* p);
 
 // device geometry of one precision (one allocation, carved into arrays)
 template <class T>
@@ -48,6 +50,7 @@ struct crn_grid {
   void* vjp_buf = nullptr;         // VJP face contributions (allocated by the first VJP call)
   float* shadow = nullptr;         // FP32 shadow of the master state (FP32_BULK)
   crn::NkWork* nk = nullptr;       // Newton-Krylov workspace (allocated by the first NK call)
+  crn::HostPipe* pipe = nullptr;   // host-buffer staging (allocated by the first host batch)
   int64_t last_bad_cell = -1;
   int32_t last_launches = 0;
   crn::LaunchCfg cfg;

@@ -55,6 +55,7 @@ struct Phys {
   T fa, fb;        // outer ghost: rho, p and B_r factors (r_I / r_G)^a, ^b
   T fbp, fvr, fvp; // outer ghost: B_phi, V_r and V_phi factors
   T psi_out;       // outer ghost psi = psi_out * psi_I (-1: psi_b = 0, +1: zero-gradient)
+  T psi_damp;      // GLM damping rate alpha: source -alpha psi in the psi equation (0: off)
   int inner_bc;    // inner boundary: 0 low-E, 1 large-E, 2 low-E with the V_r* magnitude
   double vr_star;  // large-E prescribed radial outflow
 };

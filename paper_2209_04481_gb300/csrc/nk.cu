@@ -504,6 +504,35 @@ struct Ctx {
     ++evals;
     if (err == cudaSuccess) err = e;
   }
+  int mode = 0;  // 0: y - J(dtau . y) (pseudo-time step), 1: J^T (dtau . y) (adjoint)
+
+  void apply(const double* v, double* wout, const double* U, double b_rel, bool central) {
+    if (mode == 1) adjoint_op(v, wout);
+    else apply_op(v, wout, U, b_rel, central);
+  }
+
+  // w_out = J^T (dtau . v) by the hand-written VJP of the residual; on FP32-bulk
+  // grids ut holds the FP32 copy of U and the cotangent goes through rm / rt
+  void adjoint_op(const double* v, double* wout) {
+    precond_kernel<<<w->nblk, NKB, 0, st>>>(v, w->dtau, N, w->z, nullptr, nullptr, 0.0, w->part, w->nblk,
+                                            rows.minr, 0);
+    ++launches;
+    int nl = 0;
+    cudaError_t e;
+    if (g->d.precision == CRN_FP64) {
+      e = launch_vjp_fp64(g, (const double*)w->ut, w->z, wout, nullptr, st, &nl);
+    } else {
+      perturb_kernel<float><<<grid, NKB, 0, st>>>(w->z, nullptr, nullptr, 0.0, n, (float*)w->rm);
+      ++launches;
+      e = launch_vjp_fp32(g, (const float*)w->ut, (const float*)w->rm, (float*)w->rt, nullptr, st, &nl);
+      widen_kernel<<<grid, NKB, 0, st>>>((const float*)w->rt, n, wout);
+      ++launches;
+    }
+    launches += nl;
+    ++evals;
+    if (err == cudaSuccess) err = e;
+  }
+
   // w_out = v - J (dtau . v), J by a forward or central difference
   void apply_op(const double* v, double* wout, const double* U, double b_rel, bool central) {
     precond_kernel<<<w->nblk, NKB, 0, st>>>(v, w->dtau, N, w->z, U, w->out + rows.sumabs,
@@ -577,7 +606,7 @@ double gmres(Ctx& c, const double* U, const crn_nk_options& o, double b_rel, dou
       scale_kernel<<<c.grid, NKB, 0, c.st>>>(w->V, w->b, 1.0 / beta, c.n);
       ++c.launches;
     } else {
-      c.apply_op(w->x, w->w, U, b_rel, central);
+      c.apply(w->x, w->w, U, b_rel, central);
       sub_kernel<<<c.grid, NKB, 0, c.st>>>(w->w, w->b, w->w, c.n);
       ++c.launches;
       beta = c.norm(w->w);
@@ -593,7 +622,7 @@ double gmres(Ctx& c, const double* U, const crn_nk_options& o, double b_rel, dou
     for (int j = 0; j < m; ++j) {
       double* vj = w->V + (size_t)j * c.n;
       double* vn = w->V + (size_t)(j + 1) * c.n;
-      c.apply_op(vj, vn, U, b_rel, central);
+      c.apply(vj, vn, U, b_rel, central);
       ++iters;
       // classical Gram-Schmidt, repeated once if the norm dropped by > 0.7
       c.dots(j + 1, vn, true);
@@ -797,6 +826,64 @@ int check_grid(crn_grid* g) {
   return CRN_OK;
 }
 
+// adjoint solve J^T lambda = gbar at U (GMRES on J^T diag(dt), lambda = dt . y)
+// and the sensitivity s = -(dR/dB_b)^T lambda
+int adjoint_solve(crn_grid* g, const double* U, const double* gbar, double* lambda, double* sens,
+                  const crn_nk_options& o, crn_nk_stats* out, cudaStream_t st, int& launches) {
+  cudaError_t e = ensure_work(g, o.krylov_dim);
+  if (e == cudaSuccess && !g->vjp_buf) e = cudaMalloc(&g->vjp_buf, vjp_scratch_bytes(g));
+  if (e != cudaSuccess) return report(CRN_E_CUDA, std::string("adjoint workspace: ") + cudaGetErrorString(e));
+  Ctx c(g, st);
+  c.mode = 1;
+  NkWork* w = c.w;
+  if (g->d.precision == CRN_FP64) {
+    local_dt_kernel<double><<<c.grid, NKB, 0, st>>>(g->shape, g->g64.geo, g->d.gamma, g->d.c_h, U, 1.0, w->dtau);
+    cudaMemcpyAsync(w->ut, U, sizeof(double) * c.n, cudaMemcpyDeviceToDevice, st);
+  } else {
+    local_dt_kernel<float><<<c.grid, NKB, 0, st>>>(g->shape, g->g32.geo, g->d.gamma, g->d.c_h, U, 1.0, w->dtau);
+    perturb_kernel<float><<<c.grid, NKB, 0, st>>>(U, nullptr, nullptr, 0.0, c.n, (float*)w->ut);
+    ++c.launches;
+  }
+  ++c.launches;
+  cudaMemcpyAsync(w->b, gbar, sizeof(double) * c.n, cudaMemcpyDeviceToDevice, st);
+  const double bnorm = c.norm(w->b);
+  if (!c.ok()) return report(CRN_E_CUDA, std::string("adjoint solve: ") + cudaGetErrorString(c.err));
+  int iters = 0;
+  const double rel = gmres(c, U, o, 0.0, bnorm, iters);
+  // lambda = dt . y
+  precond_kernel<<<w->nblk, NKB, 0, st>>>(w->x, w->dtau, c.N, w->z, nullptr, nullptr, 0.0, w->part, w->nblk,
+                                          c.rows.minr, 0);
+  ++c.launches;
+  if (lambda) cudaMemcpyAsync(lambda, w->z, sizeof(double) * c.n, cudaMemcpyDeviceToDevice, st);
+  if (sens) {
+    // (dR/dB_b)^T lambda from one more VJP, then negated
+    int nl = 0;
+    if (g->d.precision == CRN_FP64) {
+      e = launch_vjp_fp64(g, (const double*)w->ut, w->z, w->w, sens, st, &nl);
+    } else {
+      perturb_kernel<float><<<c.grid, NKB, 0, st>>>(w->z, nullptr, nullptr, 0.0, c.n, (float*)w->rm);
+      ++c.launches;
+      e = launch_vjp_fp32(g, (const float*)w->ut, (const float*)w->rm, (float*)w->rt, sens, st, &nl);
+    }
+    c.launches += nl;
+    ++c.evals;
+    if (c.err == cudaSuccess) c.err = e;
+    const int64_t nb = (int64_t)g->shape.nt * g->shape.np * (g->d.inner_bc == CRN_INNER_LARGE_E ? 2 : 1);
+    scale_kernel<<<(unsigned)((nb + NKB - 1) / NKB), NKB, 0, st>>>(sens, sens, -1.0, nb);
+    ++c.launches;
+  }
+  if (!c.ok()) return report(CRN_E_CUDA, std::string("adjoint solve: ") + cudaGetErrorString(c.err));
+  launches += c.launches;
+  if (out) {
+    out->res_l2 = bnorm;
+    out->lin_rel = rel;
+    out->alpha = 0.0;
+    out->krylov_iters = iters;
+    out->residual_evals = c.evals;
+  }
+  return CRN_OK;
+}
+
 }  // namespace
 }  // namespace crn
 
@@ -916,6 +1003,24 @@ int crn_steady_solve(crn_grid* g, double* U64_dev, const crn_steady_options* opt
   }
   g->last_launches = launches;
   if (stats) *stats = s;
+  return rc;
+}
+
+int crn_adjoint_solve(crn_grid* g, const double* U64_dev, const double* gbar_dev, double* lambda_dev,
+                      double* sens_dev, const crn_nk_options* opt, crn_nk_stats* stats, void* stream) {
+  int rc = crn::check_grid(g);
+  if (rc != CRN_OK) return rc;
+  if (!U64_dev || !gbar_dev || !crn::device_ptr(U64_dev) || !crn::device_ptr(gbar_dev))
+    return crn::report(CRN_E_ARG, "U64_dev and gbar_dev must be device pointers");
+  if ((lambda_dev && !crn::device_ptr(lambda_dev)) || (sens_dev && !crn::device_ptr(sens_dev)))
+    return crn::report(CRN_E_ARG, "lambda_dev and sens_dev must be device pointers");
+  crn_nk_options o;
+  if (opt) o = *opt; else crn_nk_options_default(&o);
+  rc = crn::check_nk_options(o);
+  if (rc != CRN_OK) return rc;
+  int launches = 0;
+  rc = crn::adjoint_solve(g, U64_dev, gbar_dev, lambda_dev, sens_dev, o, stats, (cudaStream_t)stream, launches);
+  g->last_launches = launches;
   return rc;
 }
 

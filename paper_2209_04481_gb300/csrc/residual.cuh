@@ -300,7 +300,7 @@ residual_cellwise(Shape sh, Geo<T> g, Phys<T> ph, const double* __restrict__ Br,
       for (int v = 0; v < NV; ++v) acc[v] += sgn * f[v];
       lam_sum += la;
     }
-    // ---- divide by the volume, gravity source [Sect. 2.2]
+    // ---- divide by the volume, gravity source [Sect. 2.2], GLM damping
     const T vol = g.rv[k] * g.av[j];
     const T ivol = one / vol;
     T r[NV];
@@ -313,6 +313,7 @@ residual_cellwise(Shape sh, Geo<T> g, Phys<T> ph, const double* __restrict__ Br,
     r[2] += rho * gy;
     r[3] += rho * gz;
     r[7] += rho * (wc[1] * gx + wc[2] * gy + wc[3] * gz);
+    r[8] -= ph.psi_damp * wc[8];
     double chk = 0.0;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
@@ -770,6 +771,7 @@ __device__ __forceinline__ void tiled_item(const Shape& sh, const Geo<T>& g, con
       r[2] += wc[0] * gy;
       r[3] += wc[0] * gz;
       r[7] += wc[0] * (wc[1] * gx + wc[2] * gy + wc[3] * gz);
+      r[8] -= ph.psi_damp * wc[8];
       const int64_t cell = (int64_t)k * cs + ocol;
       T chk = (T)0;
 #pragma unroll

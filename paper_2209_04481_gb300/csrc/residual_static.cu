@@ -103,6 +103,7 @@ int validate_static(const crn_grid_desc* d) {
     return fail(CRN_E_ARG, "bad boundary-law field");
   if (!std::isfinite(d->vr_star) || !std::isfinite(d->outer_bphi_exp) || !std::isfinite(d->outer_vphi_exp))
     return fail(CRN_E_ARG, "vr_star and the outer exponents must be finite");
+  if (!(std::isfinite(d->psi_damp) && d->psi_damp >= 0.0)) return fail(CRN_E_ARG, "psi_damp must be >= 0");
   if (d->r_last != 0.0)
     return fail(CRN_E_ARG, "crn_residual_static takes the geometric radial faces only (r_last = 0)");
   return CRN_OK;
@@ -225,6 +226,7 @@ crn::Phys<T> phys_static(const crn_grid_desc& d) {
   ph.fvr = d.outer_vr_mass ? (T)std::pow(rI / rG, 2.0 - d.outer_rho_exp) : (T)1;
   ph.fvp = (T)std::pow(rI / rG, d.outer_vphi_exp);
   ph.psi_out = d.outer_psi_extrap ? (T)1 : (T)-1;
+  ph.psi_damp = (T)d.psi_damp;
   ph.inner_bc = d.inner_bc;
   ph.vr_star = d.vr_star;
   return ph;

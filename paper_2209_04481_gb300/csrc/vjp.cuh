@@ -544,6 +544,7 @@ vjp_cells(Shape sh, Geo<T> g, Phys<T> ph, const double* __restrict__ Br, const T
   ub[1] += Rb[7 * N + c] * gx;
   ub[2] += Rb[7 * N + c] * gy;
   ub[3] += Rb[7 * N + c] * gz;
+  ub[8] -= ph.psi_damp * Rb[8 * N + c];  // S_psi = -alpha psi
 #pragma unroll
   for (int v = 0; v < NV; ++v) Ub[v * N + c] = ub[v];
 }

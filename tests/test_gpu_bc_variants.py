@@ -34,6 +34,8 @@ VARIANTS["large_e"] = dict(inner_bc="large_e", vr_star=VR_STAR)
 VARIANTS["large_e+case9"] = dict(inner_bc="large_e", vr_star=VR_STAR, **table2_params("9"))
 VARIANTS["low_e_wp"] = dict(inner_bc="low_e_wp", vr_star=VR_STAR)
 VARIANTS["low_e_wp+case9"] = dict(inner_bc="low_e_wp", vr_star=VR_STAR, **table2_params("9"))
+# GLM damping of the cleaning scalar (source -alpha psi)
+VARIANTS["psi_damp"] = dict(psi_damp=0.5)
 # the Sect. 4.3 mesh: domain to 25 R_sun with a thin outermost cell
 VARIANTS["thin_last+case1"] = dict(r_out=25.0, r_last=24.95, **table2_params("1"))
 VARIANTS["thin_last+case9"] = dict(r_out=25.0, r_last=24.95, **table2_params("9"))
@@ -116,7 +118,7 @@ def test_boundary_efield(variant, precision):
         assert np.max(np.abs(E)) <= tol * scale
 
 
-@pytest.mark.parametrize("variant", ["large_e", "case9", "case5", "large_e+case9", "low_e_wp", "low_e_wp+case9"])
+@pytest.mark.parametrize("variant", ["large_e", "case9", "case5", "large_e+case9", "low_e_wp", "low_e_wp+case9", "psi_damp"])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
 def test_vjp_dot_product(variant, precision, tol):
     """<Rbar, J v> (oracle dual numbers) = <J^T Rbar, v> (GPU VJP), including

@@ -70,7 +70,7 @@ def test_newton_krylov_option_defaults(lib):
     assert lib.crn_steady_solve(None, None, None, None, None, 0, None) == 1
 
 
-@pytest.mark.parametrize("field,value", [("inner_bc", 3), ("r_last", 0.5), ("r_last", 30.0)])
+@pytest.mark.parametrize("field,value", [("inner_bc", 3), ("r_last", 0.5), ("r_last", 30.0), ("psi_damp", -1.0)])
 def test_create_rejects_bad_boundary_fields(lib, field, value):
     d = pg.GridDesc()
     lib.crn_grid_desc_default(ctypes.byref(d), 8, 8, 16)

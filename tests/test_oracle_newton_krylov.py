@@ -113,3 +113,44 @@ def test_backward_euler_large_cfl_is_newton():
     e1, e2 = np.linalg.norm(d1 - newton), np.linalg.norm(d2 - newton)
     assert e1 < 1e-3 * np.linalg.norm(newton)
     assert 1.8 < e1 / e2 < 2.2      # first order in 1/CFL
+
+
+def test_steady_sensitivity_matches_finite_differences_of_steady_states():
+    """dg = -gbar . J^-1 (dR/dB dB) at a steady state R(U*, B) = 0 against
+    (g(U*(B + e dB)) - g(U*(B - e dB))) / 2e, the steady states found by
+    pseudo-transient continuation (backward-Euler steps, Sect. 2.1) and
+    polished by Newton with the dense Jacobian (6 x 6 x 12 shell, low-E with
+    the V_r* magnitude, dipole; g = mean outer-layer density)."""
+    shape = (6, 6, 12)
+    g = oracle_grid(shape, inner_bc="low_e_wp", vr_star=1935.07 / ci.V_REF)
+    U, info = ci.background(*shape)
+    Br = ci.magnetogram(6, 12, dipole_only=True)
+    gm1 = g.gamma - 1.0
+
+    def newton(U, Br, steps):
+        for _ in range(steps):
+            R = oracle.residual(g, U, Br)["R"]
+            U = U + np.linalg.solve(oracle.jacobian(g, U, Br), -R.ravel()).reshape(U.shape)
+        return U
+
+    cfl, r0 = 2.0, None
+    for it in range(150):
+        if it and it % 10 == 0:
+            cfl = min(2 * cfl, 128.0)
+        dU, R = oracle.backward_euler_step(g, U, Br, cfl, solver="gmres", rtol=1e-4)
+        r0 = r0 or np.linalg.norm(R)
+        if np.linalg.norm(R) < 1e-6 * r0:
+            break
+        W = oracle.cons_to_prim(g, U)
+        rho, V, B, p = W[0], W[1:4], W[4:7], W[7]
+        dp = gm1 * (dU[7] - np.sum(V * dU[1:4], 0) + 0.5 * np.sum(V * V, 0) * dU[0] - np.sum(B * dU[4:7], 0))
+        U = U + min(1.0, 0.3 / max(np.max(np.abs(dU[0]) / rho), np.max(np.abs(dp) / p))) * dU
+    U = newton(U, Br, 4)
+    assert np.linalg.norm(oracle.residual(g, U, Br)["R"]) < 1e-12
+    gbar = np.zeros_like(U)
+    gbar[0, -1] = 1.0 / (6 * 12)
+    dB = np.random.default_rng(1).standard_normal(Br.shape)
+    s = oracle.steady_sensitivity(g, U, Br, gbar, dB, rtol=1e-11)
+    e = 1e-5
+    fd = (np.sum(gbar * newton(U, Br + e * dB, 2)) - np.sum(gbar * newton(U, Br - e * dB, 2))) / (2 * e)
+    assert abs(fd - s) <= 1e-5 * abs(s)

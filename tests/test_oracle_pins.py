@@ -605,3 +605,23 @@ def test_reference_constants():
     assert ci.RHO_REF == ref["rho_ref_kg_m3"] and ci.B_REF == ref["B_ref_T"]
     # the printed V_ref is 6.7 % below B_ref / sqrt(mu0 rho_ref); the reading uses the latter
     assert abs(ci.V_REF / ref["V_ref_printed_m_s"] - 1.067) < 0.001
+
+
+def test_glm_damping_source():
+    """psi damping (rate alpha): a uniform state with psi = c in a periodic box
+    has R_psi = -alpha c exactly and no other residual; the JVP of R_psi with
+    respect to psi is -alpha."""
+    g = oracle.box(4, 4, 4, psi_damp=0.7)
+    W = np.zeros((9,) + g.shape)
+    W[0], W[7], W[8] = 1.2, 0.5, 0.3
+    W[1:4] = np.array([0.2, -0.1, 0.4])[:, None, None, None]
+    W[4:7] = np.array([0.5, 0.3, 0.1])[:, None, None, None]
+    U = ci.prim_to_cons(W, g.gamma)
+    R = oracle.residual(g, U)["R"]
+    np.testing.assert_allclose(R[8], -0.7 * 0.3, rtol=1e-14)
+    assert np.abs(R[:8]).max() < 1e-14
+    dU = np.zeros_like(U)
+    dU[8] = 1.0
+    _, dR = oracle.residual_jvp(g, U, None, dU, None)
+    np.testing.assert_allclose(dR[8], -0.7, rtol=1e-14)
+    assert np.abs(dR[:8]).max() < 1e-13
