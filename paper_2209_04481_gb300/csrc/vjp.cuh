@@ -330,7 +330,43 @@ struct VjpBufs {
   T* cr;  // r faces     (nr + 1) * nt * np
   T* ct;  // theta faces nr * (nt + 1) * np
   T* cp;  // phi faces   nr * nt * np
+  T* W;   // primitives of every cell [NV][N], recovered once per VJP (FP64 grids;
+          // null on FP32-bulk grids, whose cheap recovery is redone per stencil)
 };
+
+// pass 0: W = primitives of U (the same recovery as the forward kernels)
+template <class T>
+__global__ void __launch_bounds__(256)
+vjp_prims(Shape sh, Phys<T> ph, const T* __restrict__ U, T* __restrict__ W) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= sh.ncell) return;
+  T w[NV];
+  load_recover(U, sh.ncell, c, ph, w);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) W[v * sh.ncell + c] = w[v];
+}
+
+// primitive state of cell (k, j, i) from W, ghosts included (as cell_prim)
+template <class T>
+__device__ void cell_w(const Shape& sh, const Geo<T>& g, const Phys<T>& ph, const double* __restrict__ Br,
+                       const T* __restrict__ W, int k, int j, int i, T (&w)[NV]) {
+  map_column(j, i, sh.nt, sh.np);
+  const int64_t col = (int64_t)j * sh.np + i;
+  const int64_t cs = (int64_t)sh.nt * sh.np;
+  const int kk = k < 0 ? 0 : (k >= sh.nr ? sh.nr - 1 : k);
+  T wi[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) wi[v] = W[v * sh.ncell + (int64_t)kk * cs + col];
+  if (k < 0) {
+    inner_ghost_at(wi, Br, col, cs, (double)g.rhat[col], (double)g.rhat[cs + col],
+                   (double)g.rhat[2 * cs + col], ph, w);
+  } else if (k >= sh.nr) {
+    outer_ghost(wi, g.rhat[col], g.rhat[cs + col], g.rhat[2 * cs + col], ph, w);
+  } else {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) w[v] = wi[v];
+  }
+}
 
 template <class T>
 __device__ __forceinline__ void put_contrib(T* buf, int64_t nf, int64_t f, int pos, const T (&c)[NV]) {
@@ -410,7 +446,10 @@ vjp_faces(Shape sh, Geo<T> g, Phys<T> ph, const double* __restrict__ Br, const T
   auto cell = [&](const int (&c)[3], int shift, T (&w)[NV]) {
     int cc[3] = {c[0], c[1], c[2]};
     cc[axis] += shift;
-    cell_prim(sh, g, ph, Br, U, cc[0], cc[1], cc[2], w);
+    if (out.W)
+      cell_w(sh, g, ph, Br, out.W, cc[0], cc[1], cc[2], w);
+    else
+      cell_prim(sh, g, ph, Br, U, cc[0], cc[1], cc[2], w);
   };
   cell(lo, 0, wl);
   cell(up, 0, wr);

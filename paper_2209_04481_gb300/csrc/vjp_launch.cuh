@@ -16,7 +16,8 @@ template <> inline const Phys<float>& vphys<float>(const crn_grid* g) { return g
 
 inline size_t vjp_scratch_elems(const Shape& s) {
   const size_t cs = (size_t)s.nt * s.np;
-  return (size_t)4 * NV * ((size_t)(s.nr + 1) * cs + (size_t)s.nr * (s.nt + 1) * s.np + (size_t)s.nr * cs);
+  return (size_t)4 * NV * ((size_t)(s.nr + 1) * cs + (size_t)s.nr * (s.nt + 1) * s.np + (size_t)s.nr * cs) +
+         (size_t)NV * s.ncell;
 }
 
 template <class T, int LIM>
@@ -29,6 +30,10 @@ cudaError_t vjp_lim(crn_grid* g, const T* U, const T* Rb, T* Ub, double* Brb, cu
   b.cr = base;
   b.ct = b.cr + (size_t)4 * NV * (sh.nr + 1) * cs;
   b.cp = b.ct + (size_t)4 * NV * sh.nr * (sh.nt + 1) * sh.np;
+  // FP64: recover the primitives once (each FP64 division is costly); FP32:
+  // recovery inside the face pass is cheaper than one more pass over memory
+  b.W = sizeof(T) == 8 ? b.cp + (size_t)4 * NV * sh.nr * cs : nullptr;
+  if (b.W) vjp_prims<T><<<(unsigned)((sh.ncell + 255) / 256), 256, 0, st>>>(sh, vphys<T>(g), U, b.W);
   const int64_t nf[3] = {(int64_t)(sh.nr + 1) * (int64_t)cs, (int64_t)sh.nr * (sh.nt + 1) * sh.np,
                          (int64_t)sh.nr * (int64_t)cs};
   for (int axis = 0; axis < 3; ++axis) {
@@ -37,7 +42,7 @@ cudaError_t vjp_lim(crn_grid* g, const T* U, const T* Rb, T* Ub, double* Brb, cu
   }
   const unsigned nbc = (unsigned)((sh.ncell + 127) / 128);
   vjp_cells<T><<<nbc, 128, 0, st>>>(sh, vgeo<T>(g), vphys<T>(g), g->br, U, Rb, b, Ub, Brb);
-  *nl = 4;
+  *nl = b.W ? 5 : 4;
   return cudaGetLastError();
 }
 
