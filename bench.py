@@ -39,7 +39,8 @@ KERNEL_SOURCES = ["paper_2209_04481_gb300/csrc/residual.cuh",
                   "paper_2209_04481_gb300/csrc/mhd_device.cuh",
                   "paper_2209_04481_gb300/csrc/residual_launch.cuh",
                   "paper_2209_04481_gb300/csrc/residual_fp32.cu",
-                  "paper_2209_04481_gb300/build.py"]  # compile flags
+                  "paper_2209_04481_gb300/build.py",   # compile flags
+                  "paper_2209_04481_gb300/csrc/corona_internal.h"]  # launch configuration
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "residual_tiled_fp32_shell128.md")
 
 

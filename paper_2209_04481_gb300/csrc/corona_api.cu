@@ -328,7 +328,7 @@ int crn_grid_create(const crn_grid_desc* d, crn_grid** out) {
   g->ph64 = make_phys<double>(*d, h);
   g->ph32 = make_phys<float>(*d, h);
   // opt the kernels in to their shared memory, then size the tiled launch:
-  // radial chunk such that all CTAs fit in one wave of resident CTAs
+  // radial chunk from the makespan model over the resident CTA slots
   e = d->precision == CRN_FP64 ? crn::prepare_fp64() : crn::prepare_fp32();
   if (e != cudaSuccess) { delete g; return cuda_fail(e, "kernel attributes"); }
   {
@@ -338,7 +338,7 @@ int crn_grid_create(const crn_grid_desc* d, crn_grid** out) {
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, g->device);
     const int per_sm = d->precision == CRN_FP64 ? crn::tiled_ctas_per_sm_fp64(d->limiter)
                                                  : crn::tiled_ctas_per_sm_fp32(d->limiter);
-    int kc = crn::choose_kchunk(d->n_r, ntiles, (long long)std::max(nsm, 1) * std::max(per_sm, 1));
+    int kc = crn::choose_kchunk_balanced(d->n_r, ntiles, (long long)std::max(nsm, 1) * std::max(per_sm, 1));
     if (const char* env = std::getenv("CRN_KCHUNK")) {  // tuning override
       const int v = std::atoi(env);
       if (v >= 1) kc = v;

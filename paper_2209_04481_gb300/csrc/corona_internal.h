@@ -5,6 +5,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <functional>
+#include <vector>
+
 #include "../../include/corona.h"
 #include "mhd_device.cuh"
 
@@ -115,6 +119,44 @@ inline int choose_kchunk(int nr, long long ntiles, long long slots) {
   if (nch > nr) nch = nr;
   int kc = (int)((nr + nch - 1) / nch);
   return kc < 4 ? (nr < 4 ? nr : 4) : kc;
+}
+
+// Radial planes per CTA of the tiled kernel from a makespan model: the CTAs
+// of each candidate chunk, in launch order (all tiles of chunk 0, then chunk
+// 1, ...), are list-scheduled onto `slots` resident CTAs, each taking its
+// planes plus `overhead` planes of preamble; the chunk with the shortest
+// makespan wins (ties: the larger chunk).  Unlike one full wave, this lets
+// the short last chunks run in the gaps the full ones leave (on 128 x 64 x 128:
+// 14 planes, 288 full CTAs + 32 two-plane CTAs, beats 15 planes in one wave).
+inline int choose_kchunk_balanced(int nr, long long ntiles, long long slots, int overhead = 3) {
+  if (ntiles <= 0 || slots <= 0) return nr;
+  const int kmin = nr < 4 ? nr : 4;
+  int best = nr;
+  long long best_t = -1;
+  std::vector<long long> heap;
+  for (int kc = nr; kc >= kmin; --kc) {
+    const long long nch = (nr + kc - 1) / kc;
+    const long long rem = nr - (nch - 1) * kc;
+    const long long total = nch * ntiles;
+    const long long S = slots < total ? slots : total;
+    heap.assign((size_t)S, 0);  // slot free times (a min-heap)
+    long long makespan = 0;
+    for (long long y = 0; y < nch; ++y) {
+      const long long dur = (y == nch - 1 ? rem : kc) + overhead;
+      for (long long x = 0; x < ntiles; ++x) {
+        std::pop_heap(heap.begin(), heap.end(), std::greater<long long>());
+        const long long end = heap.back() + dur;
+        heap.back() = end;
+        std::push_heap(heap.begin(), heap.end(), std::greater<long long>());
+        if (end > makespan) makespan = end;
+      }
+    }
+    if (best_t < 0 || makespan < best_t) {
+      best_t = makespan;
+      best = kc;
+    }
+  }
+  return best;
 }
 
 }  // namespace crn
