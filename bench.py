@@ -422,6 +422,8 @@ def run_gb300(args):
         result["cpu_baseline"], err = cpu_baseline(U0, Br, info, R32, R64)
         result["error_vs_oracle"] = err
         result["cpu_baseline_all_cores"] = cpu_baseline_all_cores()
+        result["cpu_baseline"]["cpu_model"] = result["cpu_baseline_all_cores"]["cpu_model"] = cpu_model()
+        result["cpu_baseline"]["nproc"] = os.cpu_count()
     if rank == 0:
         print(json.dumps(result), flush=True)
     if dist is not None:
@@ -563,6 +565,26 @@ def cpu_baseline(U0, Br, info, R32=None, R64=None, budget_s=15.0):
     return cb, err
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else platform)."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
 def _oracle_worker(seed):
     """One full 128x64x128 oracle residual in a fresh process; returns its seconds."""
     import coronal_inputs as ci
@@ -641,7 +663,7 @@ def run_reference(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "cells_per_step": ncell, "parallelism": "cpu x1"},
         "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "cpu_model": cpu_model(), "nproc": os.cpu_count()},
         "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }), flush=True)
