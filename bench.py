@@ -166,11 +166,11 @@ def kernel_source_digest():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+def profile_values(path=PROFILE_SUMMARY):
+    """The `- key: value` lines of a committed ncu summary, if it was taken on
     the current kernel sources (else None)."""
     try:
-        with open(PROFILE_SUMMARY) as f:
+        with open(path) as f:
             text = f.read()
     except OSError:
         return None
@@ -181,10 +181,34 @@ def profiled_traffic():
             vals[k.strip()] = v.strip().strip("`")
     if vals.get("kernel_source_digest") != kernel_source_digest():
         return None
+    return vals
+
+
+def profiled_traffic():
+    """DRAM bytes per launch from the committed ncu summary (None if stale)."""
+    vals = profile_values()
     try:
         return float(vals["dram_bytes_per_launch"])
-    except (KeyError, ValueError):
+    except (KeyError, TypeError, ValueError):
         return None
+
+
+def alu_roofline():
+    """Pipe-level figures of the committed ncu summaries: the FP32 kernel's
+    instruction-issue and FMA-pipe utilisation, the FP64 kernel's FP64-pipe
+    utilisation (fractions of each unit's peak; None where a summary is stale)."""
+    out = {"source": "ncu --set full captures summarised in profiles/ (same kernel sources)"}
+    v32 = profile_values()
+    v64 = profile_values(os.path.join(ROOT, "profiles", "residual_tiled_fp64_shell128.md"))
+    for key, vals, name in (("fp32_issue_frac", v32, "issue_active_frac"),
+                            ("fp32_fma_pipe_frac", v32, "fma_pipe_frac"),
+                            ("fp64_fp64_pipe_frac", v64, "fp64_pipe_frac")):
+        try:
+            out[key] = float(vals[name])
+        except (KeyError, TypeError, ValueError):
+            out[key] = None
+    out["bound"] = "issue (FP32 kernel); FP64 pipe (FP64 kernel)"
+    return out
 
 
 def measured_peaks():
@@ -407,6 +431,7 @@ def run_gb300(args):
                    "timing": "one CUDA graph of all timed steps, CUDA events on the launch stream",
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline,
+        "alu_roofline": alu_roofline(),
         "hbm_gbs": achieved,
         "e2e": e2e,
         "gpu_launches": steps,
