@@ -108,6 +108,14 @@ typedef struct crn_grid crn_grid;
  * Returns CRN_E_ARG if d is NULL. */
 int crn_grid_desc_default(crn_grid_desc* d, int32_t n_r, int32_t n_theta, int32_t n_phi);
 
+/* Radial planes per CTA that crn_grid_create gives the tiled residual: the
+ * chunk whose CTAs, list-scheduled in launch order (all `ntiles` (theta, phi)
+ * tiles of chunk 0, then chunk 1, ...) onto `slots` resident CTAs, each costing
+ * its planes plus `overhead` planes (crn_grid_create uses 3), finish first;
+ * ties go to the larger chunk; at least 4 planes (n_r if smaller).  Pure host
+ * function; -1 on a non-positive argument. */
+int32_t crn_tiled_radial_chunk(int32_t n_r, int64_t ntiles, int64_t slots, int32_t overhead);
+
 /* Create a grid on the current CUDA device: validates *d (CRN_E_ARG with a
  * message on any bad field), computes the exact face-area vectors and volumes
  * of the shell on the host in FP64 as 1D radial factors times per-column

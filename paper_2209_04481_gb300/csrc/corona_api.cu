@@ -311,6 +311,11 @@ int crn_grid_desc_default(crn_grid_desc* d, int32_t n_r, int32_t n_theta, int32_
   return CRN_OK;
 }
 
+int32_t crn_tiled_radial_chunk(int32_t n_r, int64_t ntiles, int64_t slots, int32_t overhead) {
+  if (n_r < 1 || ntiles < 1 || slots < 1 || overhead < 0) return -1;
+  return crn::choose_kchunk_balanced(n_r, ntiles, slots, overhead);
+}
+
 int crn_grid_create(const crn_grid_desc* d, crn_grid** out) {
   if (!out) return fail(CRN_E_ARG, "out is NULL");
   *out = nullptr;

@@ -86,3 +86,38 @@ def test_ensemble_arguments_checked_on_the_host(lib):
     assert lib.crn_ensemble_residual(None, None, None, None, None, None) == 1
     assert lib.crn_ensemble_set_kchunk(None, 4) == 1
     assert lib.crn_ensemble_destroy(None) == 0
+
+
+def _makespan(nr, ntiles, slots, kc, overhead):
+    """List scheduling of the tiled launch, written independently of the library."""
+    import heapq
+    nch = -(-nr // kc)
+    rem = nr - (nch - 1) * kc
+    free = [0] * min(slots, nch * ntiles)
+    heapq.heapify(free)
+    end = 0
+    for y in range(nch):
+        dur = (rem if y == nch - 1 else kc) + overhead
+        for _ in range(ntiles):
+            t = heapq.heappop(free) + dur
+            end = max(end, t)
+            heapq.heappush(free, t)
+    return end
+
+
+@pytest.mark.parametrize("nr,ntiles,slots", [(128, 32, 304), (128, 32, 152), (96, 18, 304), (32, 2, 304),
+                                             (192, 72, 304), (48, 3, 152), (3, 4, 10)])
+def test_radial_chunk_minimises_the_makespan(lib, nr, ntiles, slots):
+    f = lib.crn_tiled_radial_chunk
+    f.restype = ctypes.c_int32
+    f.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32]
+    kc = f(nr, ntiles, slots, 3)
+    kmin = min(nr, 4)
+    spans = {k: _makespan(nr, ntiles, slots, k, 3) for k in range(kmin, nr + 1)}
+    best = min(spans.values())
+    assert spans[kc] == best and kc == max(k for k, v in spans.items() if v == best)
+    if (nr, ntiles, slots) == (128, 32, 304):
+        assert kc == 14          # measured fastest on the 128x64x128 FP32 workload
+    if (nr, ntiles, slots) == (128, 32, 152):
+        assert kc == 29
+    assert f(0, 1, 1, 3) == -1
