@@ -251,7 +251,10 @@ typedef struct {
   double max_rel_change;   /* step limiter omega; <= 0 disables it (default 0.3)    */
   int32_t fd_central;      /* 1: central difference (two residuals per product),
                               0: forward difference (default 1)                     */
-  int32_t reserved_;       /* 0                                                     */
+  int32_t precond;         /* right preconditioner: 0 scales by dtau (a Jacobi step
+                              of the local time steps, default), 1 solves the radial
+                              line-implicit tridiagonal (Rusanov dissipation part of
+                              D - J along each radial column)                        */
 } crn_nk_options;
 
 typedef struct {

@@ -7,7 +7,12 @@
 //   dt_c = V_c / sum_f max(|V_c . n_f| + c_f(W_c, n_f), c_h) |S_f|,
 //
 // solved by restarted GMRES on the right-preconditioned operator
-// y -> y - J (dtau . y) (dU = dtau . y), with the Jacobian-vector product
+// y -> (D - J) P^-1 y (dU = P^-1 y) with P = diag(1/dtau) (P^-1 y = dtau . y) or
+// P the radial line-implicit approximation of (D - J): per radial column a
+// tridiagonal of the diagonal D + (1/V) sum_f lambda_f |S_f| / 2 and the
+// couplings -lambda_r |S_r| / (2 V) to the radial neighbours, the Rusanov
+// dissipation part of the Jacobian, solved by the Thomas algorithm; the
+// Jacobian-vector product
 // taken from residual evaluations of this library,
 //   J z ~ (R(U + eps z) - R(U - eps z)) / (2 eps)   (or the forward difference),
 // eps = min(b min_e (|u_e| + s_v(e)) / |z_e|, min_c p_c / (4 |dp_lin,c(z)|)),
@@ -171,12 +176,13 @@ precond_kernel(const double* __restrict__ v, const double* __restrict__ dtau, in
     for (int q = 0; q < NV; ++q) s[q] = 1e-3 * (sumabs[q] + tot / NV) / (double)N;
   }
   for (int64_t c = (int64_t)blockIdx.x * NKB + threadIdx.x; c < N; c += stride) {
-    const double d = dtau[c];
+    // dtau null: v already is the direction z (statistics only)
+    const double d = dtau ? dtau[c] : 1.0;
     double zz[NV];
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
       zz[q] = d * v[q * N + c];
-      z[q * N + c] = zz[q];
+      if (dtau) z[q * N + c] = zz[q];
     }
     if (!want_min) continue;
     double u[NV];
@@ -236,11 +242,16 @@ perturb_kernel(const double* __restrict__ U, const double* __restrict__ z,
 template <class T>
 __global__ void __launch_bounds__(NKB)
 jvp_combine_kernel(const double* __restrict__ v, const T* __restrict__ rp, const T* __restrict__ rb,
-                   const double* __restrict__ eps, double div, int64_t n, double* __restrict__ w) {
+                   const double* __restrict__ eps, double div, int64_t n, double* __restrict__ w,
+                   const double* __restrict__ dinv = nullptr, const double* __restrict__ z = nullptr,
+                   int64_t N = 1) {
   const double ie = 1.0 / (div * *eps);
   const int64_t stride = (int64_t)gridDim.x * NKB;
-  for (int64_t e = (int64_t)blockIdx.x * NKB + threadIdx.x; e < n; e += stride)
-    w[e] = (v ? v[e] : 0.0) - ((double)rp[e] - (double)rb[e]) * ie;
+  for (int64_t e = (int64_t)blockIdx.x * NKB + threadIdx.x; e < n; e += stride) {
+    // with dinv: the D z term of (D - J) z for a general right preconditioner
+    const double first = dinv ? dinv[e % N] * z[e] : (v ? v[e] : 0.0);
+    w[e] = first - ((double)rp[e] - (double)rb[e]) * ie;
+  }
 }
 
 __global__ void __launch_bounds__(NKB)
@@ -358,6 +369,90 @@ local_dt_kernel(Shape sh, Geo<T> g, double gamma, double ch, const double* __res
   }
 }
 
+// coefficients of the radial line preconditioner P ~ (D - J): per cell the
+// D entry dinv = 1/dtau, the diagonal dinv + (1/V) sum_f lambda_f |S_f| / 2 and
+// the couplings -lambda_r |S_r| / (2 V) to the radial neighbours (the Rusanov
+// dissipation part of dR/dU), lambda from the cell's own state as for dt_c
+template <class T>
+__global__ void __launch_bounds__(NKB)
+line_coef_kernel(Shape sh, Geo<T> g, double gamma, double ch, const double* __restrict__ U, double cfl,
+                 double* __restrict__ dinv, double* __restrict__ di, double* __restrict__ lo,
+                 double* __restrict__ up) {
+  const int64_t N = sh.ncell;
+  const int64_t cs = (int64_t)sh.nt * sh.np;
+  const int64_t ts = (int64_t)(sh.nt + 1) * sh.np;
+  const int64_t stride = (int64_t)gridDim.x * NKB;
+  for (int64_t c = (int64_t)blockIdx.x * NKB + threadIdx.x; c < N; c += stride) {
+    const int i = (int)(c % sh.np);
+    const int j = (int)((c / sh.np) % sh.nt);
+    const int k = (int)(c / cs);
+    const int64_t col = (int64_t)j * sh.np + i;
+    double rho, v[3], b[3], p;
+    prim_of(U, N, c, gamma - 1.0, rho, v, b, p);
+    const double ir = 1.0 / rho;
+    const double a2 = gamma * p * ir;
+    const double b2 = (b[0] * b[0] + b[1] * b[1] + b[2] * b[2]) * ir;
+    auto lam = [&](double nx, double ny, double nz) {
+      const double un = v[0] * nx + v[1] * ny + v[2] * nz;
+      const double bn = b[0] * nx + b[1] * ny + b[2] * nz;
+      const double s = a2 + b2;
+      const double disc = fmax(s * s - 4.0 * a2 * bn * bn * ir, 0.0);
+      return fmax(fabs(un) + sqrt(0.5 * (s + sqrt(disc))), ch);
+    };
+    const double lr = lam((double)g.nr[col], (double)g.nr[cs + col], (double)g.nr[2 * cs + col]);
+    const double slo = lr * (double)g.ra[k] * (double)g.ar[j];
+    const double sup = lr * (double)g.ra[k + 1] * (double)g.ar[j];
+    double sum = slo + sup;
+    for (int jf = j; jf <= j + 1; ++jf) {
+      const double area = (double)g.rb[k] * (double)g.at[jf];
+      if (area == 0.0) continue;
+      const int64_t fc = (int64_t)jf * sh.np + i;
+      sum += lam((double)g.nth[fc], (double)g.nth[ts + fc], (double)g.nth[2 * ts + fc]) * area;
+    }
+    for (int ifc = i; ifc <= i + 1; ++ifc) {
+      const int iw = ifc % sh.np;
+      sum += lam((double)g.nph[iw], (double)g.nph[sh.np + iw], 0.0) * (double)g.rb[k] * (double)g.dtheta;
+    }
+    const double iv = 1.0 / ((double)g.rv[k] * (double)g.av[j]);
+    dinv[c] = sum * iv / cfl;
+    di[c] = dinv[c] + 0.5 * sum * iv;
+    lo[c] = k > 0 ? -0.5 * slo * iv : 0.0;
+    up[c] = k < sh.nr - 1 ? -0.5 * sup * iv : 0.0;
+  }
+}
+
+// z = P^-1 v along every radial column (Thomas algorithm, the nine variables
+// share the tridiagonal); one thread per column; cp: N doubles of scratch
+__global__ void __launch_bounds__(NKB)
+line_solve_kernel(Shape sh, const double* __restrict__ lo, const double* __restrict__ di,
+                  const double* __restrict__ up, const double* __restrict__ v, double* __restrict__ z,
+                  double* __restrict__ cp) {
+  const int64_t cs = (int64_t)sh.nt * sh.np, N = sh.ncell;
+  const int64_t col = (int64_t)blockIdx.x * NKB + threadIdx.x;
+  if (col >= cs) return;
+  double zp[NV];
+  {
+    const double m = di[col];
+    cp[col] = up[col] / m;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) { zp[q] = v[q * N + col] / m; z[q * N + col] = zp[q]; }
+  }
+  for (int k = 1; k < sh.nr; ++k) {
+    const int64_t c = (int64_t)k * cs + col;
+    const double a = lo[c];
+    const double m = di[c] - a * cp[c - cs];
+    cp[c] = up[c] / m;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) { zp[q] = (v[q * N + c] - a * zp[q]) / m; z[q * N + c] = zp[q]; }
+  }
+  for (int k = sh.nr - 2; k >= 0; --k) {
+    const int64_t c = (int64_t)k * cs + col;
+    const double f = cp[c];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) { zp[q] = z[q * N + c] - f * zp[q]; z[q * N + c] = zp[q]; }
+  }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -378,6 +473,7 @@ struct NkWork {
   void* rb = nullptr;      // n of T: base residual (FP32 grids) / R(U - eps z) (FP64 grids)
   void* rm = nullptr;      // n of T: R(U - eps z) (FP32 grids)
   double* dtau = nullptr;  // N
+  double* line = nullptr;  // 5N: radial line preconditioner (dinv, diag, lower, upper, scratch)
   double* part = nullptr;  // rows x nblk partials
   double* out = nullptr;   // rows reduced values
   double* coef = nullptr;  // m + 2 coefficients
@@ -388,6 +484,7 @@ void nk_free(NkWork* w) {
   if (!w) return;
   cudaFree(w->V); cudaFree(w->z); cudaFree(w->x); cudaFree(w->b); cudaFree(w->w);
   cudaFree(w->ut); cudaFree(w->rt); cudaFree(w->rb); cudaFree(w->rm); cudaFree(w->dtau);
+  cudaFree(w->line);
   cudaFree(w->part); cudaFree(w->out); cudaFree(w->coef);
   cudaFreeHost(w->host);
   delete w;
@@ -433,6 +530,7 @@ cudaError_t ensure_work(crn_grid* g, int m) {
   if (e == cudaSuccess) e = cudaMalloc(&w->rb, es * n);
   if (e == cudaSuccess && es == 4) e = cudaMalloc(&w->rm, es * n);
   if (e == cudaSuccess) e = cudaMalloc(&w->dtau, sizeof(double) * N);
+  if (e == cudaSuccess) e = cudaMalloc(&w->line, sizeof(double) * 5 * N);
   if (e == cudaSuccess) e = cudaMalloc(&w->part, sizeof(double) * (size_t)w->rows * w->nblk);
   if (e == cudaSuccess) e = cudaMalloc(&w->out, sizeof(double) * w->rows);
   if (e == cudaSuccess) e = cudaMalloc(&w->coef, sizeof(double) * (m + 2));
@@ -505,6 +603,15 @@ struct Ctx {
     if (err == cudaSuccess) err = e;
   }
   int mode = 0;  // 0: y - J(dtau . y) (pseudo-time step), 1: J^T (dtau . y) (adjoint)
+  int precond = 0;  // mode 0: 0 scales by dtau, 1 solves the radial line preconditioner
+
+  // z = P^-1 v (radial lines); w->line holds dinv, diag, lower, upper, scratch
+  void line_solve(const double* v, double* z) {
+    const double* L = w->line;
+    const unsigned nb = (unsigned)((g->shape.nt * (int64_t)g->shape.np + NKB - 1) / NKB);
+    line_solve_kernel<<<nb, NKB, 0, st>>>(g->shape, L + 2 * N, L + N, L + 3 * N, v, z, w->line + 4 * N);
+    ++launches;
+  }
 
   void apply(const double* v, double* wout, const double* U, double b_rel, bool central) {
     if (mode == 1) adjoint_op(v, wout);
@@ -535,9 +642,16 @@ struct Ctx {
 
   // w_out = v - J (dtau . v), J by a forward or central difference
   void apply_op(const double* v, double* wout, const double* U, double b_rel, bool central) {
-    precond_kernel<<<w->nblk, NKB, 0, st>>>(v, w->dtau, N, w->z, U, w->out + rows.sumabs,
-                                            g->d.gamma - 1.0, w->part, w->nblk, rows.minr, 1);
+    if (precond == 1) {
+      line_solve(v, w->z);
+      precond_kernel<<<w->nblk, NKB, 0, st>>>(w->z, nullptr, N, w->z, U, w->out + rows.sumabs,
+                                              g->d.gamma - 1.0, w->part, w->nblk, rows.minr, 1);
+    } else {
+      precond_kernel<<<w->nblk, NKB, 0, st>>>(v, w->dtau, N, w->z, U, w->out + rows.sumabs,
+                                              g->d.gamma - 1.0, w->part, w->nblk, rows.minr, 1);
+    }
     ++launches;
+    const double* dinv = precond == 1 ? w->line : nullptr;
     finish(rows.minr, 2, 2);
     eps_kernel<<<1, 1, 0, st>>>(w->out, rows.minr, rows.eps, b_rel);
     ++launches;
@@ -554,7 +668,7 @@ struct Ctx {
         base = (const double*)w->rb;
       }
       jvp_combine_kernel<double><<<grid, NKB, 0, st>>>(v, (const double*)w->rt, base, e,
-                                                       central ? 2.0 : 1.0, n, wout);
+                                                       central ? 2.0 : 1.0, n, wout, dinv, w->z, N);
     } else {
       perturb_kernel<float><<<grid, NKB, 0, st>>>(U, w->z, e, 1.0, n, (float*)w->ut);
       ++launches;
@@ -567,7 +681,7 @@ struct Ctx {
         base = (const float*)w->rm;
       }
       jvp_combine_kernel<float><<<grid, NKB, 0, st>>>(v, (const float*)w->rt, base, e,
-                                                      central ? 2.0 : 1.0, n, wout);
+                                                      central ? 2.0 : 1.0, n, wout, dinv, w->z, N);
     }
     ++launches;
   }
@@ -707,6 +821,7 @@ int nk_step(crn_grid* g, double* U, double cfl, const crn_nk_options& o, crn_nk_
   cudaError_t e = ensure_work(g, o.krylov_dim);
   if (e != cudaSuccess) return report(CRN_E_CUDA, std::string("Newton-Krylov workspace: ") + cudaGetErrorString(e));
   Ctx c(g, st);
+  c.precond = o.precond;
   NkWork* w = c.w;
   const double b_rel = o.fd_rel > 0.0 ? o.fd_rel : default_b(g, o.fd_central != 0);
   const double gm1 = g->d.gamma - 1.0;
@@ -719,6 +834,16 @@ int nk_step(crn_grid* g, double* U, double cfl, const crn_nk_options& o, crn_nk_
       local_dt_kernel<double><<<c.grid, NKB, 0, st>>>(g->shape, g64, g->d.gamma, g->d.c_h, U, cfl, w->dtau);
     else
       local_dt_kernel<float><<<c.grid, NKB, 0, st>>>(g->shape, g->g32.geo, g->d.gamma, g->d.c_h, U, cfl, w->dtau);
+    ++c.launches;
+  }
+  if (o.precond == 1) {
+    double* L = w->line;
+    if (g->d.precision == CRN_FP64)
+      line_coef_kernel<double><<<c.grid, NKB, 0, st>>>(g->shape, g->g64.geo, g->d.gamma, g->d.c_h, U, cfl, L,
+                                                       L + c.N, L + 2 * c.N, L + 3 * c.N);
+    else
+      line_coef_kernel<float><<<c.grid, NKB, 0, st>>>(g->shape, g->g32.geo, g->d.gamma, g->d.c_h, U, cfl, L,
+                                                      L + c.N, L + 2 * c.N, L + 3 * c.N);
     ++c.launches;
   }
   absmean_kernel<<<w->nblk, NKB, 0, st>>>(U, c.N, w->part, w->nblk, c.rows.sumabs);
@@ -749,10 +874,14 @@ int nk_step(crn_grid* g, double* U, double cfl, const crn_nk_options& o, crn_nk_
   }
   int iters = 0;
   const double rel = gmres(c, U, o, b_rel, bnorm, iters);
-  // dU = dtau . y
-  precond_kernel<<<w->nblk, NKB, 0, st>>>(w->x, w->dtau, c.N, w->z, U, w->out + c.rows.sumabs, gm1,
-                                          w->part, w->nblk, c.rows.minr, 0);
-  ++c.launches;
+  // dU = P^-1 y (dtau . y, or the radial line solve)
+  if (o.precond == 1) {
+    c.line_solve(w->x, w->z);
+  } else {
+    precond_kernel<<<w->nblk, NKB, 0, st>>>(w->x, w->dtau, c.N, w->z, U, w->out + c.rows.sumabs, gm1,
+                                            w->part, w->nblk, c.rows.minr, 0);
+    ++c.launches;
+  }
   // step length: relative-change limiter, then positivity
   double alpha = 1.0;
   if (o.max_rel_change > 0.0) {
@@ -805,6 +934,7 @@ int check_nk_options(const crn_nk_options& o) {
     return report(CRN_E_ARG, "fd_rel must be in [0, 0.1)");
   if (!std::isfinite(o.max_rel_change)) return report(CRN_E_ARG, "max_rel_change must be finite");
   if (o.fd_central != 0 && o.fd_central != 1) return report(CRN_E_ARG, "fd_central must be 0 or 1");
+  if (o.precond != 0 && o.precond != 1) return report(CRN_E_ARG, "precond must be 0 or 1");
   return CRN_OK;
 }
 

@@ -147,3 +147,32 @@ def test_strong_field_start_drains_a_cell():
         assert "CRN_E_NONPHYSICAL" in str(e)
     W = oracle.cons_to_prim(og, U64.cpu().numpy())
     assert W[0].min() > 0 and W[7].min() > 0
+
+
+@pytest.mark.parametrize("bc,cfl", [("low_e", 2.0), ("large_e", 2.0), ("low_e_wp", 2.0), ("large_e", 20.0),
+                                    ("low_e_wp", 200.0)])
+def test_one_step_with_the_radial_line_preconditioner(bc, cfl):
+    """The preconditioner changes how GMRES gets there, not the step: dU still
+    matches the oracle's direct solve of the same system (FP64, 1e-5)."""
+    shape = (6, 8, 16)
+    g, U, Br, og = setup(shape, bc, "fp64", seed=5)
+    ref, _ = oracle.backward_euler_step(og, U, Br, cfl, solver="dense")
+    U64 = torch.from_numpy(U).cuda()
+    dU = torch.empty_like(U64)
+    st = g.newton_krylov_step(U64, cfl, dU=dU, krylov_dim=300, max_restarts=4, lin_rtol=1e-10,
+                              max_rel_change=0.0, precond=1)
+    g.sync_status()
+    err = per_var_err(dU.cpu().numpy(), ref)
+    assert np.all(err <= 1e-5), (err, st)
+
+
+def test_steady_solve_with_the_radial_line_preconditioner():
+    shape = (32, 16, 32)
+    g, U, Br, og = setup(shape, "low_e_wp", "fp64", dipole_only=True)
+    U64 = torch.from_numpy(U).cuda()
+    stats, hist = g.steady_solve(U64, max_steps=300, tol_drop=1e-6, nk=dict(precond=1))
+    g.sync_status()
+    assert stats["converged"] == 1, (stats, hist[-5:])
+    r0 = np.linalg.norm(oracle.residual(og, U, Br)["R"])
+    r1 = np.linalg.norm(oracle.residual(og, U64.cpu().numpy(), Br)["R"])
+    assert r1 <= 2e-6 * r0
