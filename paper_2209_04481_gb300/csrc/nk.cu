@@ -18,8 +18,9 @@
 // eps = min(b min_e (|u_e| + s_v(e)) / |z_e|, min_c p_c / (4 |dp_lin,c(z)|)),
 // so that no entry of the state moves by more than the fraction b of its own
 // size (s_v = 1e-3 x (the mean |u| of its variable + the mean |u| over all
-// nine variables)) and no cell's pressure by more than a quarter.  The step is then limited to a relative change of rho and of
-// the linearised p of at most omega per cell, and halved while any cell of
+// nine variables)) and no cell's pressure by more than a quarter.  The step is
+// then limited to a relative change of rho and of the linearised p of at most
+// omega per cell, and halved while any cell of
 // U + alpha dU would have rho <= 0 or p <= 0.  The CFL law of Sect. 4.1
 // (start at 2, double every few steps, up to 128) drives crn_steady_solve.
 //

@@ -119,3 +119,37 @@ def test_ensemble_rejects_mixed_members():
     e = pg.Ensemble([a])
     with pytest.raises(pg.CoronaError, match="set_inner_boundary"):
         e.residual([torch.zeros((9, 8, 8, 16), device="cuda")])
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_ensemble_launches_replay_from_a_cuda_graph(precision):
+    """After one call has uploaded the member records, ensemble residual calls
+    (a counter memset and the persistent kernel) capture into a CUDA graph whose
+    replay gives exactly the direct call's R and norms."""
+    import paper_2209_04481_gb300 as pg
+    gs, Us, Brs = members(precision)
+    Ud = [torch.from_numpy(U).to("cuda", gs[0].dtype) for U in Us]
+    n = len(gs)
+    ens = pg.Ensemble(gs)
+    norms = torch.zeros((n, 9), dtype=torch.float64, device="cuda")
+    ref = [R.clone() for R in ens.residual(Ud, norms=norms)]
+    ref_norms = norms.clone()
+    torch.cuda.synchronize()   # calls on other streams must not overlap this one
+    Rs = [torch.zeros_like(u) for u in Ud]
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ens.residual(Ud, Rs, norms=norms, stream=s)   # uploads the records for these buffers
+    s.synchronize()
+    for R in Rs:
+        R.zero_()
+    norms.zero_()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        for _ in range(3):
+            ens.residual(Ud, Rs, norms=norms, stream=s)
+    graph.replay()
+    torch.cuda.synchronize()
+    for m in range(n):
+        assert torch.equal(Rs[m], ref[m]), m
+    assert torch.equal(norms, ref_norms)
+    gs[0].sync_status()
