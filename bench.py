@@ -463,20 +463,27 @@ def run_nk(torch, pg, ci, device, stream):
     vr = 1935.07 / ci.V_REF
     out = {"note": "dipole start (the strong-field l<=15 start drains a base cell to vacuum under "
                    "any pseudo-time schedule); inner_bc low_e_wp; wall-clock seconds"}
-    for name, shape, precision, tol, max_steps in (("shell32_fp64", (32, 16, 32), "fp64", 1e-6, 300),
-                                                   ("shell96_fp32", (96, 48, 96), "fp32", 1e-6, 150)):
+    # (name, shape, precision, limiter, drop, max steps, CFL cap, Newton-Krylov options)
+    runs = (("shell32_fp64", (32, 16, 32), "fp64", "vanalbada", 1e-6, 300, 128.0, {}),
+            # SURVEY config 4: minmod, CFL up to 1024, radial line preconditioner, GMRES(60)
+            ("shell96_fp64_minmod", (96, 48, 96), "fp64", "minmod", 1e-6, 300, 1024.0,
+             {"precond": 1, "krylov_dim": 60}))
+    for name, shape, precision, limiter, tol, max_steps, cfl_max, nkopt in runs:
         U, info = ci.background(*shape)
         Br = ci.magnetogram(shape[1], shape[2], dipole_only=True)
-        g = pg.Grid(*shape, precision=precision, p_b=info["p_b"], inner_bc="low_e_wp", vr_star=vr)
+        g = pg.Grid(*shape, precision=precision, limiter=limiter, p_b=info["p_b"], inner_bc="low_e_wp",
+                    vr_star=vr)
         g.set_inner_boundary(torch.from_numpy(Br).to(device))
         U64 = torch.from_numpy(U).to(device)
         torch.cuda.synchronize(device)
         t0 = time.perf_counter()
         with torch.cuda.stream(stream):
-            st, _ = g.steady_solve(U64, max_steps=max_steps, tol_drop=tol, stream=stream)
+            st, _ = g.steady_solve(U64, max_steps=max_steps, tol_drop=tol, cfl_max=cfl_max, nk=nkopt,
+                                   stream=stream)
         torch.cuda.synchronize(device)
         sec = time.perf_counter() - t0
-        out[name] = {"shape": list(shape), "seconds": sec, "steps": st["steps"],
+        out[name] = {"shape": list(shape), "limiter": limiter, "cfl_max": cfl_max, "nk_options": nkopt,
+                     "seconds": sec, "steps": st["steps"],
                      "residual_evals": st["residual_evals"], "krylov_iters": st["krylov_iters"],
                      "converged": bool(st["converged"]), "tol_drop": tol,
                      "drop": st["res_final"] / st["res0"], "max_steps": max_steps,
