@@ -496,7 +496,7 @@ def run_nk(torch, pg, ci, device, stream):
             t0 = time.perf_counter()
             with torch.cuda.stream(stream):
                 _, _, ast = g.adjoint_solve(U64, gbar, stream=stream, krylov_dim=100, max_restarts=3,
-                                            lin_rtol=1e-8)
+                                            lin_rtol=1e-8, precond=1)
             torch.cuda.synchronize(device)
             out[name]["adjoint"] = {"functional": "mean outer-layer density", "seconds": time.perf_counter() - t0,
                                     "krylov_iters": ast["krylov_iters"], "vjp_evals": ast["residual_evals"],

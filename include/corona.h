@@ -358,7 +358,9 @@ int32_t crn_ensemble_launch_count(const crn_ensemble* e);
  * device) by GMRES on J^T diag(dt_c) with the hand-written VJP of
  * crn_residual_vjp, and writes sens_dev = dg/dB_b = -(dR/dB_b)^T lambda
  * (FP64, the shape crn_set_inner_boundary takes) and, if lambda_dev is not
- * NULL, lambda.  opt: krylov_dim, max_restarts and lin_rtol are used.  The
+ * NULL, lambda.  opt: krylov_dim, max_restarts, lin_rtol and precond are used
+ * (precond 1: the transposed radial line preconditioner, the lines of
+ * crn_nk_options.precond at infinite CFL, negated and transposed).  The
  * first call allocates the Newton-Krylov and VJP workspaces.  Synchronises
  * `stream` once or twice per Krylov step. */
 int crn_adjoint_solve(crn_grid* g, const double* U64_dev, const double* gbar_dev, double* lambda_dev,

@@ -424,6 +424,27 @@ line_coef_kernel(Shape sh, Geo<T> g, double gamma, double ch, const double* __re
 
 // z = P^-1 v along every radial column (Thomas algorithm, the nine variables
 // share the tridiagonal); one thread per column; cp: N doubles of scratch
+// the adjoint's preconditioner P_a = -(L)^T ~ J^T from the forward line
+// coefficients taken at infinite CFL (L = diag, lower, upper in slots 1, 2, 3):
+// lower_T(k) = -upper(k - 1) -> slot 0, upper_T(k) = -lower(k + 1) -> slot 5,
+// diag_T = -diag in place
+__global__ void __launch_bounds__(NKB)
+line_transpose_kernel(Shape sh, double* __restrict__ L) {
+  const int64_t N = sh.ncell, cs = (int64_t)sh.nt * sh.np;
+  const int64_t stride = (int64_t)gridDim.x * NKB;
+  for (int64_t c = (int64_t)blockIdx.x * NKB + threadIdx.x; c < N; c += stride) {
+    const int k = (int)(c / cs);
+    L[c] = k > 0 ? -L[3 * N + c - cs] : 0.0;
+    L[5 * N + c] = k < sh.nr - 1 ? -L[2 * N + c + cs] : 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(NKB)
+negate_kernel(double* __restrict__ x, int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * NKB;
+  for (int64_t e = (int64_t)blockIdx.x * NKB + threadIdx.x; e < n; e += stride) x[e] = -x[e];
+}
+
 __global__ void __launch_bounds__(NKB)
 line_solve_kernel(Shape sh, const double* __restrict__ lo, const double* __restrict__ di,
                   const double* __restrict__ up, const double* __restrict__ v, double* __restrict__ z,
@@ -474,7 +495,8 @@ struct NkWork {
   void* rb = nullptr;      // n of T: base residual (FP32 grids) / R(U - eps z) (FP64 grids)
   void* rm = nullptr;      // n of T: R(U - eps z) (FP32 grids)
   double* dtau = nullptr;  // N
-  double* line = nullptr;  // 5N: radial line preconditioner (dinv, diag, lower, upper, scratch)
+  double* line = nullptr;  // 6N: radial line preconditioner (dinv, diag, lower, upper, scratch,
+                           //     upper of the transposed lines for the adjoint)
   double* part = nullptr;  // rows x nblk partials
   double* out = nullptr;   // rows reduced values
   double* coef = nullptr;  // m + 2 coefficients
@@ -531,7 +553,7 @@ cudaError_t ensure_work(crn_grid* g, int m) {
   if (e == cudaSuccess) e = cudaMalloc(&w->rb, es * n);
   if (e == cudaSuccess && es == 4) e = cudaMalloc(&w->rm, es * n);
   if (e == cudaSuccess) e = cudaMalloc(&w->dtau, sizeof(double) * N);
-  if (e == cudaSuccess) e = cudaMalloc(&w->line, sizeof(double) * 5 * N);
+  if (e == cudaSuccess) e = cudaMalloc(&w->line, sizeof(double) * 6 * N);
   if (e == cudaSuccess) e = cudaMalloc(&w->part, sizeof(double) * (size_t)w->rows * w->nblk);
   if (e == cudaSuccess) e = cudaMalloc(&w->out, sizeof(double) * w->rows);
   if (e == cudaSuccess) e = cudaMalloc(&w->coef, sizeof(double) * (m + 2));
@@ -607,10 +629,15 @@ struct Ctx {
   int precond = 0;  // mode 0: 0 scales by dtau, 1 solves the radial line preconditioner
 
   // z = P^-1 v (radial lines); w->line holds dinv, diag, lower, upper, scratch
+  // (forward: lower, diag, upper in slots 2, 1, 3; adjoint: the transposed
+  // lines in slots 0, 1, 5); slot 4 is the Thomas scratch
   void line_solve(const double* v, double* z) {
     const double* L = w->line;
     const unsigned nb = (unsigned)((g->shape.nt * (int64_t)g->shape.np + NKB - 1) / NKB);
-    line_solve_kernel<<<nb, NKB, 0, st>>>(g->shape, L + 2 * N, L + N, L + 3 * N, v, z, w->line + 4 * N);
+    if (mode == 1)
+      line_solve_kernel<<<nb, NKB, 0, st>>>(g->shape, L, L + N, L + 5 * N, v, z, w->line + 4 * N);
+    else
+      line_solve_kernel<<<nb, NKB, 0, st>>>(g->shape, L + 2 * N, L + N, L + 3 * N, v, z, w->line + 4 * N);
     ++launches;
   }
 
@@ -622,9 +649,13 @@ struct Ctx {
   // w_out = J^T (dtau . v) by the hand-written VJP of the residual; on FP32-bulk
   // grids ut holds the FP32 copy of U and the cotangent goes through rm / rt
   void adjoint_op(const double* v, double* wout) {
-    precond_kernel<<<w->nblk, NKB, 0, st>>>(v, w->dtau, N, w->z, nullptr, nullptr, 0.0, w->part, w->nblk,
-                                            rows.minr, 0);
-    ++launches;
+    if (precond == 1) {
+      line_solve(v, w->z);
+    } else {
+      precond_kernel<<<w->nblk, NKB, 0, st>>>(v, w->dtau, N, w->z, nullptr, nullptr, 0.0, w->part, w->nblk,
+                                              rows.minr, 0);
+      ++launches;
+    }
     int nl = 0;
     cudaError_t e;
     if (g->d.precision == CRN_FP64) {
@@ -966,7 +997,20 @@ int adjoint_solve(crn_grid* g, const double* U, const double* gbar, double* lamb
   if (e != cudaSuccess) return report(CRN_E_CUDA, std::string("adjoint workspace: ") + cudaGetErrorString(e));
   Ctx c(g, st);
   c.mode = 1;
+  c.precond = o.precond;
   NkWork* w = c.w;
+  if (o.precond == 1) {
+    double* L = w->line;
+    if (g->d.precision == CRN_FP64)
+      line_coef_kernel<double><<<c.grid, NKB, 0, st>>>(g->shape, g->g64.geo, g->d.gamma, g->d.c_h, U, INFINITY,
+                                                       L, L + c.N, L + 2 * c.N, L + 3 * c.N);
+    else
+      line_coef_kernel<float><<<c.grid, NKB, 0, st>>>(g->shape, g->g32.geo, g->d.gamma, g->d.c_h, U, INFINITY,
+                                                      L, L + c.N, L + 2 * c.N, L + 3 * c.N);
+    line_transpose_kernel<<<c.grid, NKB, 0, st>>>(g->shape, L);
+    negate_kernel<<<c.grid, NKB, 0, st>>>(L + c.N, c.N);
+    c.launches += 3;
+  }
   if (g->d.precision == CRN_FP64) {
     local_dt_kernel<double><<<c.grid, NKB, 0, st>>>(g->shape, g->g64.geo, g->d.gamma, g->d.c_h, U, 1.0, w->dtau);
     cudaMemcpyAsync(w->ut, U, sizeof(double) * c.n, cudaMemcpyDeviceToDevice, st);
@@ -981,10 +1025,14 @@ int adjoint_solve(crn_grid* g, const double* U, const double* gbar, double* lamb
   if (!c.ok()) return report(CRN_E_CUDA, std::string("adjoint solve: ") + cudaGetErrorString(c.err));
   int iters = 0;
   const double rel = gmres(c, U, o, 0.0, bnorm, iters);
-  // lambda = dt . y
-  precond_kernel<<<w->nblk, NKB, 0, st>>>(w->x, w->dtau, c.N, w->z, nullptr, nullptr, 0.0, w->part, w->nblk,
-                                          c.rows.minr, 0);
-  ++c.launches;
+  // lambda = P_a^-1 y (dt . y, or the transposed line solve)
+  if (o.precond == 1) {
+    c.line_solve(w->x, w->z);
+  } else {
+    precond_kernel<<<w->nblk, NKB, 0, st>>>(w->x, w->dtau, c.N, w->z, nullptr, nullptr, 0.0, w->part, w->nblk,
+                                            c.rows.minr, 0);
+    ++c.launches;
+  }
   if (lambda) cudaMemcpyAsync(lambda, w->z, sizeof(double) * c.n, cudaMemcpyDeviceToDevice, st);
   if (sens) {
     // (dR/dB_b)^T lambda from one more VJP, then negated

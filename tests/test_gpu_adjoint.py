@@ -46,14 +46,15 @@ def objectives(shape, U):
 
 @pytest.mark.parametrize("bc", ["low_e_wp", "large_e"])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-6), ("fp32", 2e-2)])
-def test_adjoint_sensitivity_matches_oracle_tangent(bc, precision, tol):
+@pytest.mark.parametrize("precond", [0, 1])
+def test_adjoint_sensitivity_matches_oracle_tangent(bc, precision, tol, precond):
     shape = (6, 6, 16)
     g, U64, Br, og = steady(shape, bc, precision)
     U = U64.cpu().numpy()
     rng = np.random.default_rng(7)
     for name, gbar in objectives(shape, U).items():
         sens, _, st = g.adjoint_solve(U64, torch.from_numpy(gbar).cuda(), krylov_dim=300, max_restarts=5,
-                                      lin_rtol=1e-11 if precision == "fp64" else 1e-6)
+                                      lin_rtol=1e-11 if precision == "fp64" else 1e-6, precond=precond)
         g.sync_status()
         assert sens.shape == Br.shape
         s = sens.cpu().numpy()
@@ -64,13 +65,14 @@ def test_adjoint_sensitivity_matches_oracle_tangent(bc, precision, tol):
             assert abs(got - ref) <= tol * np.sum(np.abs(s * dB)), (name, got, ref, st)
 
 
-def test_adjoint_lambda_solves_the_transposed_system():
+@pytest.mark.parametrize("precond", [0, 1])
+def test_adjoint_lambda_solves_the_transposed_system(precond):
     """J^T lambda = gbar, checked with the GPU VJP itself: (dR/dU)^T lambda."""
     shape = (8, 8, 16)
     g, U64, Br, og = steady(shape, "low_e_wp", "fp64")
     gbar = torch.from_numpy(objectives(shape, None)["rho"]).cuda()
     lam = torch.empty_like(U64)
-    g.adjoint_solve(U64, gbar, lam=lam, krylov_dim=300, max_restarts=5, lin_rtol=1e-11)
+    g.adjoint_solve(U64, gbar, lam=lam, krylov_dim=300, max_restarts=5, lin_rtol=1e-11, precond=precond)
     Ub, _ = g.residual_vjp(U64, lam)
     g.sync_status()
     assert torch.linalg.vector_norm(Ub - gbar) <= 1e-8 * torch.linalg.vector_norm(gbar)
