@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--only-headline", nargs="?", const="fp32", choices=["fp32", "fp64"], default=None,
                     help="time the residual in this precision only (for profiler captures); skips "
                          "e2e, pseudo-time, VJP, Newton-Krylov and ensemble measurements")
+    ap.add_argument("--only-pseudo-time", action="store_true",
+                    help="time the FP32-bulk residual and then the explicit pseudo-time step only "
+                         "(for profiler captures of the update kernel)")
     return ap.parse_args()
 
 
@@ -242,6 +245,38 @@ def time_graph(torch, stream, fn_list, steps, warmup):
 # ---------------------------------------------------------------------------
 # the GB300 arm
 # ---------------------------------------------------------------------------
+def measure_pseudo_time(torch, g32, U0, device, stream, steps):
+    """Explicit pseudo-time update (FP32 bulk residual + FP64 master update),
+    in batches of 10 steps from the initial state (forward Euler at CFL 0.4
+    is only run for short stretches, as in the 10-step shell32 case)."""
+    ncell = U0[0].size
+    U0d = torch.from_numpy(U0.copy()).to(device)
+    U64 = U0d.clone()
+    batch, nbatch = 10, max(1, min(steps // 40, 20))
+    with torch.cuda.stream(stream):
+        g32.pseudo_time_step(U64, 3, 0.4, stream=stream)
+    stream.synchronize()
+    pts_sec = 0.0
+    for _ in range(nbatch):
+        with torch.cuda.stream(stream):
+            U64.copy_(U0d)
+            p0 = torch.cuda.Event(enable_timing=True)
+            p1 = torch.cuda.Event(enable_timing=True)
+            p0.record(stream)
+            g32.pseudo_time_step(U64, batch, 0.4, stream=stream)
+            p1.record(stream)
+        torch.cuda.synchronize(device)
+        pts_sec += p0.elapsed_time(p1) / 1e3
+    g32.sync_status(stream)
+    pts_steps = batch * nbatch
+    pts = {"value": ncell * pts_steps / pts_sec, "unit": "cell-updates/s",
+           "ms_per_step": pts_sec * 1e3 / pts_steps, "steps": pts_steps, "cfl": 0.4,
+           "launches_per_step": 2,
+           "note": "residual on the FP32 shadow + FP64 master update and res(a) monitor; "
+                   f"{nbatch} batches of {batch} steps from the initial state"}
+    return pts
+
+
 def run_gb300(args):
     import numpy as np
     import torch
@@ -301,6 +336,17 @@ def run_gb300(args):
                 "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
     R32 = Rs[(steps - 1) % N_ROTATE].double().cpu().numpy()
     del graph
+    if args.only_pseudo_time:
+        pts = measure_pseudo_time(torch, g32, U0, device, stream, steps)
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
+                              "steps": steps, "warmup": warmup, "ms_per_step": sec_max * 1e3 / steps,
+                              "higher_is_better": True, "pseudo_time_step": pts,
+                              "note": "headline and pseudo-time step only (profiling run)"}), flush=True)
+        g32.close()
+        if dist is not None:
+            dist.destroy_process_group()
+        return
     if args.only_headline:
         if args.only_headline == "fp64":
             roofline = {"bound": "alu", "note": "FP64 residual: FP64-pipe bound"}
@@ -337,35 +383,9 @@ def run_gb300(args):
            "api": "Grid.residual_host_batch -> crn_residual_host_batch (pinned host buffers, "
                   "copies of consecutive steps overlapped with the residual)"}
 
-    # ---- explicit pseudo-time update (FP32 bulk residual + FP64 master update),
-    # in batches of 10 steps from the initial state (forward Euler at CFL 0.4
-    # is only run for short stretches, as in the 10-step shell32 case)
-    U0d = torch.from_numpy(U0.copy()).to(device)
-    U64 = U0d.clone()
-    batch, nbatch = 10, max(1, min(steps // 40, 20))
-    with torch.cuda.stream(stream):
-        g32.pseudo_time_step(U64, 3, 0.4, stream=stream)
-    stream.synchronize()
-    pts_sec = 0.0
-    for _ in range(nbatch):
-        with torch.cuda.stream(stream):
-            U64.copy_(U0d)
-            p0 = torch.cuda.Event(enable_timing=True)
-            p1 = torch.cuda.Event(enable_timing=True)
-            p0.record(stream)
-            g32.pseudo_time_step(U64, batch, 0.4, stream=stream)
-            p1.record(stream)
-        torch.cuda.synchronize(device)
-        pts_sec += p0.elapsed_time(p1) / 1e3
-    g32.sync_status(stream)
-    pts_steps = batch * nbatch
-    pts = {"value": ncell * pts_steps / pts_sec, "unit": "cell-updates/s",
-           "ms_per_step": pts_sec * 1e3 / pts_steps, "steps": pts_steps, "cfl": 0.4,
-           "launches_per_step": 2,
-           "note": "residual on the FP32 shadow + FP64 master update and res(a) monitor; "
-                   f"{nbatch} batches of {batch} steps from the initial state"}
+    pts = measure_pseudo_time(torch, g32, U0, device, stream, steps)
     g32.close()
-    del Us, Rs, U64, U0d
+    del Us, Rs
 
     # ---- plain FP64 residual
     g64, Us, Rs, n64, d64, calls = make("fp64")

@@ -350,6 +350,7 @@ int crn_grid_create(const crn_grid_desc* d, crn_grid** out) {
     }
     g->cfg.kchunk_tiled = kc;
     g->cfg.num_sms = std::max(nsm, 1);
+    g->cfg.update_per_sm = crn::update_blocks_per_sm(d->precision != CRN_FP64);
     const int64_t tiled_blocks = ntiles * ((d->n_r + kc - 1) / kc);
     const int64_t cell_blocks = (g->shape.ncell + 255) / 256;
     g->max_blocks = (size_t)std::max<int64_t>(std::max<int64_t>(tiled_blocks, cell_blocks), 4 * 152 * 8);

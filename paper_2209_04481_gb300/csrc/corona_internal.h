@@ -30,6 +30,7 @@ struct GeoBuf {
 struct LaunchCfg {
   int kchunk_tiled = 16;  // radial planes per CTA of the tiled kernel
   int num_sms = 152;      // streaming multiprocessors of the grid's device
+  int update_per_sm = 2;  // resident blocks per SM of the pseudo-time update
 };
 
 }  // namespace crn
@@ -90,6 +91,7 @@ cudaError_t launch_ensemble_update(const void* dev, int nmem, int nitems, double
                                    cudaStream_t st);
 size_t ens_update_bytes();
 unsigned update_blocks(const crn_grid* g);
+int update_blocks_per_sm(bool fp32);
 void ens_update_fill(crn_grid* g, double* U64, int item0, int nitems, double* log_out, void* dst);
 cudaError_t launch_efield_fp64(crn_grid* g, const double* U, double* E, bool volume, cudaStream_t st,
                                 int* nl);

@@ -10,7 +10,13 @@
 //   dp = (gamma - 1) (dE - d(rho V^2/2) - d(B^2/2)),   d psi = dU_psi,
 // in the grid's precision, squared and summed per thread (compensated in
 // FP32), then across threads and CTAs in FP64.
+//
+// FP32-bulk grids: the FP64 pipe executes only the nine master-state FMAs
+// per cell.  Widening R and narrowing the new shadow go through the integer
+// pipe (fp_bits.cuh), and the compensated FP32 sums are combined across the
+// block in FP32 pairs before the one conversion to FP64 per block.
 #include "corona_internal.h"
+#include "fp_bits.cuh"
 #include "residual.cuh"
 
 namespace crn {
@@ -36,6 +42,87 @@ __device__ __forceinline__ void monitor_increments(const TM (&u0)[NV], const TM 
   dw[8] = du[8];
 }
 
+__device__ __forceinline__ double widen(float x) { return widen_f32(x); }
+__device__ __forceinline__ double widen(double x) { return x; }
+
+// (s, c) += (s2, c2) for compensated sums whose value is s - c: the sum of
+// the leading parts is split exactly into t + err (Knuth's TwoSum), and err
+// moves into the correction.
+__device__ __forceinline__ void pair_add(float& s, float& c, float s2, float c2) {
+  const float t = s + s2;
+  const float bp = t - s;
+  const float err = (s - (t - bp)) + (s2 - bp);
+  s = t;
+  c = (c + c2) - err;
+}
+
+// Block sum of the per-thread compensated FP32 sums (256 threads): FP32
+// pairs across each warp by shuffles, then across the eight warps by warp 0;
+// tot[] of thread 0 receives the block's totals, every other thread's tot[]
+// is zero (the form reduce_and_finalize_at<256, true> takes, which adds the
+// warps' lane-0 values).  `scratch` holds at least 8 * 2 * NV floats.
+__device__ __forceinline__ void block_sum_pairs(Acc<float>& acc, double (&tot)[NV], double* scratch) {
+  float* sp = reinterpret_cast<float*>(scratch);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const float s2 = __shfl_xor_sync(0xffffffffu, acc.s[v], off);
+      const float c2 = __shfl_xor_sync(0xffffffffu, acc.c[v], off);
+      pair_add(acc.s[v], acc.c[v], s2, c2);
+    }
+  }
+  __syncthreads();  // scratch may still be read by an earlier use
+  if (lane == 0) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      sp[(warp * NV + v) * 2] = acc.s[v];
+      sp[(warp * NV + v) * 2 + 1] = acc.c[v];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int v = 0; v < NV; ++v) tot[v] = 0.0;
+  if (warp == 0) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      float s = 0.f, c = 0.f;
+      if (lane < 8) {
+        s = sp[(lane * NV + v) * 2];
+        c = sp[(lane * NV + v) * 2 + 1];
+      }
+#pragma unroll
+      for (int off = 4; off > 0; off >>= 1) {
+        const float s2 = __shfl_xor_sync(0xffffffffu, s, off);
+        const float c2 = __shfl_xor_sync(0xffffffffu, c, off);
+        pair_add(s, c, s2, c2);
+      }
+      if (lane == 0) tot[v] = (double)s - (double)c;
+    }
+  }
+}
+
+// U^t, R and the state the monitor differences against (the FP32 shadow
+// when there is one) of cell c
+template <class TR>
+__device__ __forceinline__ void load_cell(int64_t N, int64_t c, const double* __restrict__ U,
+                                          const TR* __restrict__ R, const float* shadow_old,
+                                          double (&uo)[NV], TR (&r)[NV], TR (&u0)[NV]) {
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    uo[v] = U[v * N + c];
+    r[v] = R[v * N + c];
+  }
+  if (shadow_old) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) u0[v] = (TR)shadow_old[v * N + c];
+  } else {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) u0[v] = (TR)uo[v];
+  }
+}
+
 // TR: element type of R (double on FP64 grids, float on FP32_BULK grids);
 // the monitor arithmetic runs in the same type.
 // block `bid` of `nblocks` blocks covering the N cells of one grid
@@ -48,27 +135,39 @@ __device__ __forceinline__ void update_block(int64_t N, double* __restrict__ U, 
   const TR dtr = (TR)dt;
   Acc<TR> acc;
   acc.init();
-  for (int64_t c = (int64_t)bid * blockDim.x + threadIdx.x; c < N; c += (int64_t)nblocks * blockDim.x) {
-    TR u0[NV], du[NV], dw[NV];
+  // one cell: master-state update, new shadow, monitor increments
+  auto step = [&](int64_t c, const double (&uo)[NV], const TR (&r)[NV], const TR (&u0)[NV]) {
+    TR du[NV], dw[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      const double uo = U[v * N + c];
-      const TR r = R[v * N + c];
-      // the old shadow (if any) is read before the new one overwrites it
-      u0[v] = shadow_old ? (TR)shadow_old[v * N + c] : (TR)uo;
-      const double un = fma(dt, (double)r, uo);
+      const double un = fma(dt, widen(r[v]), uo[v]);
       U[v * N + c] = un;
-      if (shadow_new) shadow_new[v * N + c] = (float)un;
-      du[v] = dtr * r;
+      if (shadow_new) shadow_new[v * N + c] = narrow_f64(un);
+      du[v] = dtr * r[v];
     }
     monitor_increments(u0, du, gm1, dw);
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc.add(v, dw[v]);
+  };
+  // all 27 loads of a cell are issued before its first store: the old and
+  // the new shadow are one buffer, so interleaving them would serialise nine
+  // memory round trips per cell
+  const int64_t stride = (int64_t)nblocks * blockDim.x;
+  for (int64_t c = (int64_t)bid * blockDim.x + threadIdx.x; c < N; c += stride) {
+    double uo[NV];
+    TR r[NV], u0[NV];
+    load_cell(N, c, U, R, shadow_old, uo, r, u0);
+    step(c, uo, r, u0);
   }
   double tot[NV];
+  if constexpr (std::is_same<TR, float>::value) {
+    block_sum_pairs(acc, tot, scratch);
+    reduce_and_finalize_at<256, true>(tot, INFINITY, red, scratch, bid, nblocks);
+  } else {
 #pragma unroll
-  for (int v = 0; v < NV; ++v) tot[v] = acc.total(v);
-  reduce_and_finalize_at<256>(tot, INFINITY, red, scratch, bid, nblocks);
+    for (int v = 0; v < NV; ++v) tot[v] = acc.total(v);
+    reduce_and_finalize_at<256>(tot, INFINITY, red, scratch, bid, nblocks);
+  }
 }
 
 template <class TR>
@@ -145,10 +244,28 @@ shadow_kernel(int64_t n, const double* __restrict__ U, float* __restrict__ S) {
     S[q] = (float)U[q];
 }
 
+// Resident 256-thread blocks per SM of the update kernel (register bound).
+int update_blocks_per_sm(bool fp32) {
+  int n = 0;
+  const cudaError_t e = fp32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, update_kernel<float>, 256, 0)
+                             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, update_kernel<double>, 256, 0);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    n = 2;
+  }
+  return n < 1 ? 1 : n;
+}
+
+// Blocks of the update: one resident wave, grid-stride.  The closing
+// last-CTA reduction costs every block a partial, an arrival atomic on one
+// counter, and a row the last CTA reads back; on 128 x 64 x 128 each block
+// beyond the first wave cost about 17 ns, and a second wave gave no overlap
+// that paid for it.
 unsigned update_blocks(const crn_grid* g) {
   int64_t nb = (g->shape.ncell + 255) / 256;
+  const int64_t cap = (int64_t)g->cfg.update_per_sm * g->cfg.num_sms;
+  if (nb > cap) nb = cap;
   if (nb > (int64_t)g->max_blocks) nb = (int64_t)g->max_blocks;
-  if (nb > 4 * 152 * 8) nb = 4 * 152 * 8;
   return (unsigned)(nb < 1 ? 1 : nb);
 }
 

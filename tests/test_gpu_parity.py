@@ -172,6 +172,28 @@ def test_pseudo_time_steps_shell32(precision):
     np.testing.assert_allclose(res.cpu().numpy(), res_ref, atol=1e-8 if precision == "fp64" else 1e-4)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_pseudo_time_steps_one_call_equal_single_steps(precision):
+    """Within one call the update writes the next FP32 shadow itself (integer
+    narrowing, rounded to nearest even); every call starts from a shadow made
+    by the conversion instruction.  Six steps in one call and six one-step
+    calls must therefore agree bit for bit, monitor rows included."""
+    U, Br = problem("shell32")
+    shape = (32, 16, 32)
+    g = gpu_grid(shape, precision)
+    g.set_inner_boundary(torch.from_numpy(Br).cuda())
+    Ua = torch.from_numpy(U.copy()).cuda()
+    ra = torch.zeros((6, 9), dtype=torch.float64, device="cuda")
+    g.pseudo_time_step(Ua, 6, 0.4, ra)
+    Ub = torch.from_numpy(U.copy()).cuda()
+    rb = torch.zeros((6, 9), dtype=torch.float64, device="cuda")
+    for s in range(6):
+        g.pseudo_time_step(Ub, 1, 0.4, rb[s:s + 1])
+    g.sync_status()
+    assert torch.equal(Ua, Ub)
+    assert torch.equal(ra, rb)
+
+
 def test_nonphysical_state_is_reported():
     import paper_2209_04481_gb300 as pg
     shape = (8, 8, 16)
