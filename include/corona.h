@@ -83,7 +83,9 @@ typedef struct {
   double gamma;                 /* ratio of specific heats, > 1                  */
   double c_h;                   /* GLM cleaning speed, >= 0                      */
   double g0;                    /* gravity: g = -g0 rhat / r^2                   */
-  double lim_eps;               /* van Albada epsilon, >= 0                      */
+  double lim_eps;               /* van Albada epsilon: > 0 with that limiter
+                                   (its smooth form is 0/0 where both slopes
+                                   vanish), else ignored but >= 0             */
   double outer_rho_exp;         /* outer ghost rho, p scaled by (r_I/r_G)^a      */
   double outer_br_exp;          /* outer ghost B_r scaled by (r_I/r_G)^b         */
   double rho_b, p_b;            /* inner boundary density and pressure, > 0      */

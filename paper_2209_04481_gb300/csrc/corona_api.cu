@@ -58,6 +58,9 @@ int validate(const crn_grid_desc* d) {
   if (!(finite(d->c_h) && d->c_h >= 0.0)) return fail(CRN_E_ARG, "c_h must be >= 0");
   if (!finite(d->g0)) return fail(CRN_E_ARG, "g0 must be finite");
   if (!(finite(d->lim_eps) && d->lim_eps >= 0.0)) return fail(CRN_E_ARG, "lim_eps must be >= 0");
+  // the smooth van Albada form is 0/0 where both one-sided slopes vanish
+  if (d->limiter == CRN_LIM_VANALBADA && !(d->lim_eps > 0.0))
+    return fail(CRN_E_ARG, "lim_eps must be > 0 with the van Albada limiter");
   if (!finite(d->outer_rho_exp) || !finite(d->outer_br_exp))
     return fail(CRN_E_ARG, "outer exponents must be finite");
   if (!(finite(d->rho_b) && d->rho_b > 0.0 && finite(d->p_b) && d->p_b > 0.0))

@@ -38,7 +38,7 @@ def test_descriptor_defaults(lib):
 @pytest.mark.parametrize("field,value,needle", [
     ("n_phi", 12, "n_phi"), ("n_r", 1, "n_r"), ("gamma", 1.0, "gamma"),
     ("r_out", 0.5, "r_in"), ("precision", 7, "precision"), ("limiter", 9, "limiter"),
-    ("p_b", -1.0, "p_b"), ("c_h", -1.0, "c_h")])
+    ("p_b", -1.0, "p_b"), ("c_h", -1.0, "c_h"), ("lim_eps", 0.0, "van Albada")])
 def test_create_rejects_bad_descriptors_before_any_device_work(lib, field, value, needle):
     d = pg.GridDesc()
     lib.crn_grid_desc_default(ctypes.byref(d), 8, 8, 16)
