@@ -216,6 +216,10 @@ __device__ __forceinline__ void outer_ghost(const T (&wi)[NV], T ex, T ey, T ez,
 // ---------------------------------------------------------------------------
 // slope limiters on the two one-sided slopes a (backward), b (forward)
 // ---------------------------------------------------------------------------
+template <class T> __device__ __forceinline__ T fmat(T a, T b, T c);
+template <> __device__ __forceinline__ double fmat<double>(double a, double b, double c) { return fma(a, b, c); }
+template <> __device__ __forceinline__ float fmat<float>(float a, float b, float c) { return fmaf(a, b, c); }
+
 template <int LIM, class T>
 __device__ __forceinline__ T limited_slope(T a, T b, T eps) {
   if (LIM == 0) {  // unlimited central
@@ -223,10 +227,32 @@ __device__ __forceinline__ T limited_slope(T a, T b, T eps) {
   } else if (LIM == 1) {  // minmod
     const T m = fabs(a) < fabs(b) ? a : b;
     return a * b > (T)0 ? m : (T)0;
-  } else {  // van Albada, smooth form
-    const T num = a * (b * b + eps) + b * (a * a + eps);
-    const T den = a * a + b * b + (T)2 * eps;
+  } else {  // van Albada, smooth form; explicit FMAs so that every kernel
+            // inlining this rounds it the same way
+    const T num = fmat(a, fmat(b, b, eps), b * fmat(a, a, eps));
+    const T den = fmat(a, a, fmat(b, b, (T)2 * eps));
     return num * frcp(den);
+  }
+}
+
+// Two limited slopes at once.  FP64 van Albada shares one division between
+// them, 1/(d1 d2) times d2 and d1 (three multiplies and one IEEE division in
+// place of two divisions on the slow FP64 pipe); d >= 2 eps > 0 and the
+// slopes' squares keep d1 d2 far inside the binary64 range.  Every other case
+// is two calls of limited_slope.
+template <int LIM, class T>
+__device__ __forceinline__ void limited_slope2(T a1, T b1, T a2, T b2, T eps, T& s1, T& s2) {
+  if (LIM == 2 && sizeof(T) == 8) {
+    const T n1 = fmat(a1, fmat(b1, b1, eps), b1 * fmat(a1, a1, eps));
+    const T d1 = fmat(a1, a1, fmat(b1, b1, (T)2 * eps));
+    const T n2 = fmat(a2, fmat(b2, b2, eps), b2 * fmat(a2, a2, eps));
+    const T d2 = fmat(a2, a2, fmat(b2, b2, (T)2 * eps));
+    const T inv = frcp(d1 * d2);
+    s1 = n1 * (inv * d2);
+    s2 = n2 * (inv * d1);
+  } else {
+    s1 = limited_slope<LIM>(a1, b1, eps);
+    s2 = limited_slope<LIM>(a2, b2, eps);
   }
 }
 

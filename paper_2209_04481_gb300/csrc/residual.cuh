@@ -556,11 +556,22 @@ __device__ __forceinline__ void tiled_item(const Shape& sh, const Geo<T>& g, con
   auto r_values = [&](int p, const T (&wm)[NV], const T (&w0)[NV], const T (&wp)[NV], T (&lo)[NV],
                       T (&up)[NV]) {
     const T im = g.inv_dm[p], ip = g.inv_dp[p], hm = g.hm[p], hp = g.hp[p];
+    constexpr int VSTEP = sizeof(T) == 8 ? 2 : 1;  // FP64: slopes in pairs
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const T s = limited_slope<LIM>((w0[v] - wm[v]) * im, (wp[v] - w0[v]) * ip, ph.eps);
-      lo[v] = w0[v] - s * hm;
-      up[v] = w0[v] + s * hp;
+    for (int v = 0; v < NV; v += VSTEP) {
+      if (VSTEP == 2 && v + 1 < NV) {
+        T s, s1;
+        limited_slope2<LIM>((w0[v] - wm[v]) * im, (wp[v] - w0[v]) * ip, (w0[v + 1] - wm[v + 1]) * im,
+                            (wp[v + 1] - w0[v + 1]) * ip, ph.eps, s, s1);
+        lo[v] = fmat(-s, hm, w0[v]);
+        up[v] = fmat(s, hp, w0[v]);
+        lo[v + 1] = fmat(-s1, hm, w0[v + 1]);
+        up[v + 1] = fmat(s1, hp, w0[v + 1]);
+      } else {
+        const T s = limited_slope<LIM>((w0[v] - wm[v]) * im, (wp[v] - w0[v]) * ip, ph.eps);
+        lo[v] = fmat(-s, hm, w0[v]);
+        up[v] = fmat(s, hp, w0[v]);
+      }
     }
   };
 
@@ -649,12 +660,18 @@ __device__ __forceinline__ void tiled_item(const Shape& sh, const Geo<T>& g, con
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         const T* q = Pk + v * HC + hown;
-        const T st = limited_slope<LIM>(wc[v] - q[-HP], q[HP] - wc[v], ph.eps);
-        tvl[v * NTV + jj * TP + ii] = wc[v] - half * st;
-        tvu[v * NTV + (jj + 1) * TP + ii] = wc[v] + half * st;
-        const T sp = limited_slope<LIM>(wc[v] - q[-1], q[1] - wc[v], ph.eps);
-        pvl[v * NPV + jj * (TP + 1) + ii] = wc[v] - half * sp;
-        pvu[v * NPV + jj * (TP + 1) + ii + 1] = wc[v] + half * sp;
+        T st, sp;
+        if constexpr (sizeof(T) == 8) {
+          limited_slope2<LIM>(wc[v] - q[-HP], q[HP] - wc[v], wc[v] - q[-1], q[1] - wc[v], ph.eps, st, sp);
+        } else {
+          st = limited_slope<LIM>(wc[v] - q[-HP], q[HP] - wc[v], ph.eps);
+          sp = limited_slope<LIM>(wc[v] - q[-1], q[1] - wc[v], ph.eps);
+        }
+        // explicit FMAs: the same rounding in every kernel inlining this
+        tvl[v * NTV + jj * TP + ii] = fmat(-half, st, wc[v]);
+        tvu[v * NTV + (jj + 1) * TP + ii] = fmat(half, st, wc[v]);
+        pvl[v * NPV + jj * (TP + 1) + ii] = fmat(-half, sp, wc[v]);
+        pvu[v * NPV + jj * (TP + 1) + ii + 1] = fmat(half, sp, wc[v]);
       }
       // halo cells whose face values the tile's boundary faces need
       for (int e = tid; e < D::NEXTRA_V; e += NT) {
@@ -673,12 +690,22 @@ __device__ __forceinline__ void tiled_item(const Shape& sh, const Geo<T>& g, con
         }
         const bool upper = (dst == tvu) || (dst == pvu);
         const int nstride = (dst == tvu || dst == tvl) ? NTV : NPV;
+        constexpr int VSTEP = sizeof(T) == 8 ? 2 : 1;  // FP64: slopes in pairs
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
+        for (int v = 0; v < NV; v += VSTEP) {
           const T* q = Pk + v * HC + hrow * HP + hcol;
           const T w = q[0];
-          const T s = limited_slope<LIM>(w - q[-dstep], q[dstep] - w, ph.eps);
-          dst[v * nstride + idx] = upper ? w + half * s : w - half * s;
+          if (VSTEP == 2 && v + 1 < NV) {
+            const T* q1 = q + HC;
+            const T w1 = q1[0];
+            T s, s1;
+            limited_slope2<LIM>(w - q[-dstep], q[dstep] - w, w1 - q1[-dstep], q1[dstep] - w1, ph.eps, s, s1);
+            dst[v * nstride + idx] = fmat(upper ? half : -half, s, w);
+            dst[(v + 1) * nstride + idx] = fmat(upper ? half : -half, s1, w1);
+          } else {
+            const T s = limited_slope<LIM>(w - q[-dstep], q[dstep] - w, ph.eps);
+            dst[v * nstride + idx] = fmat(upper ? half : -half, s, w);
+          }
         }
       }
     }
