@@ -297,7 +297,8 @@ __device__ __forceinline__ void rusanov(const T (&wl)[NV], const T (&wr)[NV], T 
   T lam = L.sp > R.sp ? L.sp : R.sp;
   lam = lam > ph.ch ? lam : ph.ch;
   const T h = (T)0.5 * area;
-  const T d = (T)0.5 * lam * area;
+  lam_area = lam * area;
+  const T d = (T)0.5 * lam_area;  // halving is exact: the same value as (lam / 2) area
   // mass
   const T ml = wl[0] * L.un, mr = wr[0] * R.un;
   f[0] = h * (ml + mr) - d * (wr[0] - wl[0]);
@@ -322,7 +323,6 @@ __device__ __forceinline__ void rusanov(const T (&wl)[NV], const T (&wr)[NV], T 
          - d * (R.en - L.en);
   // cleaning scalar
   f[8] = h * (ph.ch2 * (L.bn + R.bn)) - d * (wr[8] - wl[8]);
-  lam_area = lam * area;
 }
 
 // across-pole / periodic mapping of a (possibly out-of-range) column (j, i):

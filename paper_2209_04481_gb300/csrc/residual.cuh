@@ -804,9 +804,8 @@ __device__ __forceinline__ void tiled_item(const Shape& sh, const Geo<T>& g, con
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         R[v * N + cell] = r[v];
-        const T r2 = r[v] * r[v];
-        sq[v] += r2;
-        chk += r2;
+        sq[v] = fmat(r[v], r[v], sq[v]);
+        chk = fmat(r[v], r[v], chk);
       }
       const T dtc = vol / lam;
       dtm = dtc < dtm ? dtc : dtm;
