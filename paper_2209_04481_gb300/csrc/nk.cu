@@ -11,7 +11,8 @@
 // P the radial line-implicit approximation of (D - J): per radial column a
 // tridiagonal of the diagonal D + (1/V) sum_f lambda_f |S_f| / 2 and the
 // couplings -lambda_r |S_r| / (2 V) to the radial neighbours, the Rusanov
-// dissipation part of the Jacobian, solved by the Thomas algorithm; the
+// dissipation part of the Jacobian, solved by the Thomas algorithm (factored
+// once per step, then one substitution per Krylov step); the
 // Jacobian-vector product
 // taken from residual evaluations of this library,
 //   J z ~ (R(U + eps z) - R(U - eps z)) / (2 eps)   (or the forward difference),
@@ -77,6 +78,9 @@ mdot_kernel(const double* __restrict__ V, int64_t n, int i0, int cnt, const doub
 #pragma unroll
   for (int t = 0; t <= MD; ++t) a[t] = 0.0;
   const int64_t stride = (int64_t)nblk * NKB;
+  // two elements per trip: their loads are in flight together, so that the
+  // FMAs (bound by the FP64 pipe) overlap the memory latency
+#pragma unroll 2
   for (int64_t e = (int64_t)blockIdx.x * NKB + threadIdx.x; e < n; e += stride) {
     const double we = w[e];
 #pragma unroll
@@ -156,6 +160,15 @@ absmean_kernel(const double* __restrict__ U, int64_t N, double* __restrict__ par
   block_sum_rows<NV>(a, part, nblk, row, NV);
 }
 
+// reciprocal good to about 20 bits (PTX rcp.approx.ftz.f64), for the ratios
+// that only set the finite-difference step: an IEEE division costs several
+// slots of the slow FP64 pipe, and the step needs its magnitude only
+__device__ __forceinline__ double rcp_coarse(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  return r;
+}
+
 // z = dtau . v (dtau per cell, shared by its nine variables).  With want_min,
 // two partial minima for the finite-difference step: over entries of
 // (|u| + s_v) / |z| into row `row`, and over cells of p / |dp_lin(z)| into
@@ -190,16 +203,16 @@ precond_kernel(const double* __restrict__ v, const double* __restrict__ dtau, in
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
       u[q] = U[q * N + c];
-      if (zz[q] != 0.0) m = fmin(m, (fabs(u[q]) + s[q]) / fabs(zz[q]));
+      if (zz[q] != 0.0) m = fmin(m, (fabs(u[q]) + s[q]) * rcp_coarse(fabs(zz[q])));
     }
-    const double ir = 1.0 / u[0];
+    const double ir = rcp_coarse(u[0]);
     const double vx = u[1] * ir, vy = u[2] * ir, vz = u[3] * ir;
     const double p = gm1 * (u[7] - 0.5 * (u[1] * vx + u[2] * vy + u[3] * vz) -
                             0.5 * (u[4] * u[4] + u[5] * u[5] + u[6] * u[6]));
     const double dp = gm1 * (zz[7] - (vx * zz[1] + vy * zz[2] + vz * zz[3]) +
                              0.5 * (vx * vx + vy * vy + vz * vz) * zz[0] -
                              (u[4] * zz[4] + u[5] * zz[5] + u[6] * zz[6]));
-    if (dp != 0.0) mp = fmin(mp, p / fabs(dp));
+    if (dp != 0.0) mp = fmin(mp, p * rcp_coarse(fabs(dp)));
   }
   if (!want_min) return;
   __shared__ double sm[2][NKB];
@@ -445,33 +458,52 @@ negate_kernel(double* __restrict__ x, int64_t n) {
   for (int64_t e = (int64_t)blockIdx.x * NKB + threadIdx.x; e < n; e += stride) x[e] = -x[e];
 }
 
+// Thomas factorisation of every radial line, once per set of coefficients:
+// m_0 = d_0, m_k = d_k - l_k c_(k-1) with c_k = u_k / m_k; stores c_k and
+// 1/m_k.  One thread per column (the recurrence runs along r).
 __global__ void __launch_bounds__(NKB)
-line_solve_kernel(Shape sh, const double* __restrict__ lo, const double* __restrict__ di,
-                  const double* __restrict__ up, const double* __restrict__ v, double* __restrict__ z,
-                  double* __restrict__ cp) {
-  const int64_t cs = (int64_t)sh.nt * sh.np, N = sh.ncell;
+line_factor_kernel(Shape sh, const double* __restrict__ lo, const double* __restrict__ di,
+                   const double* __restrict__ up, double* __restrict__ cp, double* __restrict__ im) {
+  const int64_t cs = (int64_t)sh.nt * sh.np;
   const int64_t col = (int64_t)blockIdx.x * NKB + threadIdx.x;
   if (col >= cs) return;
-  double zp[NV];
-  {
-    const double m = di[col];
-    cp[col] = up[col] / m;
-#pragma unroll
-    for (int q = 0; q < NV; ++q) { zp[q] = v[q * N + col] / m; z[q * N + col] = zp[q]; }
+  double c = 0.0;
+  for (int k = 0; k < sh.nr; ++k) {
+    const int64_t q = (int64_t)k * cs + col;
+    const double inv = 1.0 / (k == 0 ? di[q] : di[q] - lo[q] * c);
+    c = up[q] * inv;
+    cp[q] = c;
+    im[q] = inv;
   }
+}
+
+// z = P^-1 v along every radial column from the factors: forward
+// y_k = (v_k - l_k y_(k-1)) / m_k, backward z_k = y_k - c_k z_(k+1).  One
+// thread per (variable, column): the nine right-hand sides share the factors,
+// and 9 n_theta n_phi threads keep every SM busy; the loads along r do not
+// depend on the recurrence and are issued ahead of it.
+__global__ void __launch_bounds__(NKB)
+line_solve_kernel(Shape sh, const double* __restrict__ lo, const double* __restrict__ cp,
+                  const double* __restrict__ im, const double* __restrict__ v, double* __restrict__ z) {
+  const int64_t cs = (int64_t)sh.nt * sh.np, N = sh.ncell;
+  const int64_t t = (int64_t)blockIdx.x * NKB + threadIdx.x;
+  if (t >= NV * cs) return;
+  const int64_t q = t / cs, col = t - q * cs;
+  const double* __restrict__ vq = v + q * N;
+  double* __restrict__ zq = z + q * N;
+  double y = vq[col] * im[col];
+  zq[col] = y;
+#pragma unroll 4
   for (int k = 1; k < sh.nr; ++k) {
     const int64_t c = (int64_t)k * cs + col;
-    const double a = lo[c];
-    const double m = di[c] - a * cp[c - cs];
-    cp[c] = up[c] / m;
-#pragma unroll
-    for (int q = 0; q < NV; ++q) { zp[q] = (v[q * N + c] - a * zp[q]) / m; z[q * N + c] = zp[q]; }
+    y = fma(-lo[c], y, vq[c]) * im[c];
+    zq[c] = y;
   }
+#pragma unroll 4
   for (int k = sh.nr - 2; k >= 0; --k) {
     const int64_t c = (int64_t)k * cs + col;
-    const double f = cp[c];
-#pragma unroll
-    for (int q = 0; q < NV; ++q) { zp[q] = z[q * N + c] - f * zp[q]; z[q * N + c] = zp[q]; }
+    y = fma(-cp[c], y, zq[c]);
+    zq[c] = y;
   }
 }
 
@@ -495,8 +527,9 @@ struct NkWork {
   void* rb = nullptr;      // n of T: base residual (FP32 grids) / R(U - eps z) (FP64 grids)
   void* rm = nullptr;      // n of T: R(U - eps z) (FP32 grids)
   double* dtau = nullptr;  // N
-  double* line = nullptr;  // 6N: radial line preconditioner (dinv, diag, lower, upper, scratch,
-                           //     upper of the transposed lines for the adjoint)
+  double* line = nullptr;  // 7N: radial line preconditioner (dinv, diag, lower, upper, the
+                           //     factors c_k, upper of the transposed lines for the adjoint,
+                           //     the inverse pivots 1/m_k)
   double* part = nullptr;  // rows x nblk partials
   double* out = nullptr;   // rows reduced values
   double* coef = nullptr;  // m + 2 coefficients
@@ -540,7 +573,7 @@ cudaError_t ensure_work(crn_grid* g, int m) {
   g->nk = w;
   w->m = m;
   w->n = n;
-  w->nblk = 2 * g->cfg.num_sms;
+  w->nblk = 4 * g->cfg.num_sms;
   w->rows = Rows(m).total;
   const size_t es = g->d.precision == CRN_FP64 ? 8 : 4;
   cudaError_t e = cudaMalloc(&w->V, sizeof(double) * (size_t)(m + 1) * n);
@@ -553,7 +586,7 @@ cudaError_t ensure_work(crn_grid* g, int m) {
   if (e == cudaSuccess) e = cudaMalloc(&w->rb, es * n);
   if (e == cudaSuccess && es == 4) e = cudaMalloc(&w->rm, es * n);
   if (e == cudaSuccess) e = cudaMalloc(&w->dtau, sizeof(double) * N);
-  if (e == cudaSuccess) e = cudaMalloc(&w->line, sizeof(double) * 6 * N);
+  if (e == cudaSuccess) e = cudaMalloc(&w->line, sizeof(double) * 7 * N);
   if (e == cudaSuccess) e = cudaMalloc(&w->part, sizeof(double) * (size_t)w->rows * w->nblk);
   if (e == cudaSuccess) e = cudaMalloc(&w->out, sizeof(double) * w->rows);
   if (e == cudaSuccess) e = cudaMalloc(&w->coef, sizeof(double) * (m + 2));
@@ -628,16 +661,23 @@ struct Ctx {
   int mode = 0;  // 0: y - J(dtau . y) (pseudo-time step), 1: J^T (dtau . y) (adjoint)
   int precond = 0;  // mode 0: 0 scales by dtau, 1 solves the radial line preconditioner
 
-  // z = P^-1 v (radial lines); w->line holds dinv, diag, lower, upper, scratch
-  // (forward: lower, diag, upper in slots 2, 1, 3; adjoint: the transposed
-  // lines in slots 0, 1, 5); slot 4 is the Thomas scratch
-  void line_solve(const double* v, double* z) {
-    const double* L = w->line;
+  // w->line: dinv, diag, lower, upper (forward: lower, diag, upper in slots 2,
+  // 1, 3; adjoint: the transposed lines in slots 0, 1, 5); the Thomas factors
+  // c_k in slot 4 and 1/m_k in slot 6 (line_factor)
+  void line_factor() {
+    double* L = w->line;
     const unsigned nb = (unsigned)((g->shape.nt * (int64_t)g->shape.np + NKB - 1) / NKB);
     if (mode == 1)
-      line_solve_kernel<<<nb, NKB, 0, st>>>(g->shape, L, L + N, L + 5 * N, v, z, w->line + 4 * N);
+      line_factor_kernel<<<nb, NKB, 0, st>>>(g->shape, L, L + N, L + 5 * N, L + 4 * N, L + 6 * N);
     else
-      line_solve_kernel<<<nb, NKB, 0, st>>>(g->shape, L + 2 * N, L + N, L + 3 * N, v, z, w->line + 4 * N);
+      line_factor_kernel<<<nb, NKB, 0, st>>>(g->shape, L + 2 * N, L + N, L + 3 * N, L + 4 * N, L + 6 * N);
+    ++launches;
+  }
+  // z = P^-1 v (radial lines, from the factors)
+  void line_solve(const double* v, double* z) {
+    const double* L = w->line;
+    const unsigned nb = (unsigned)((NV * g->shape.nt * (int64_t)g->shape.np + NKB - 1) / NKB);
+    line_solve_kernel<<<nb, NKB, 0, st>>>(g->shape, mode == 1 ? L : L + 2 * N, L + 4 * N, L + 6 * N, v, z);
     ++launches;
   }
 
@@ -877,6 +917,7 @@ int nk_step(crn_grid* g, double* U, double cfl, const crn_nk_options& o, crn_nk_
       line_coef_kernel<float><<<c.grid, NKB, 0, st>>>(g->shape, g->g32.geo, g->d.gamma, g->d.c_h, U, cfl, L,
                                                       L + c.N, L + 2 * c.N, L + 3 * c.N);
     ++c.launches;
+    c.line_factor();
   }
   absmean_kernel<<<w->nblk, NKB, 0, st>>>(U, c.N, w->part, w->nblk, c.rows.sumabs);
   ++c.launches;
@@ -1010,6 +1051,7 @@ int adjoint_solve(crn_grid* g, const double* U, const double* gbar, double* lamb
     line_transpose_kernel<<<c.grid, NKB, 0, st>>>(g->shape, L);
     negate_kernel<<<c.grid, NKB, 0, st>>>(L + c.N, c.N);
     c.launches += 3;
+    c.line_factor();
   }
   if (g->d.precision == CRN_FP64) {
     local_dt_kernel<double><<<c.grid, NKB, 0, st>>>(g->shape, g->g64.geo, g->d.gamma, g->d.c_h, U, 1.0, w->dtau);
