@@ -242,7 +242,8 @@ int crn_efield(crn_grid* g, const void* U_dev, double* E_dev, void* stream);
  * cell's linearised pressure by more than a quarter.  U is then advanced by alpha dU, alpha = min(1,
  * max_rel_change / max_c max(|d rho|/rho, |dp_lin|/p)) (dp_lin the linearised
  * pressure change), halved while any cell would get rho <= 0 or p <= 0.
- * All vectors are FP64 on the device; reductions are deterministic. */
+ * All vectors are FP64 on the device (the Krylov basis FP32 if basis_fp32
+ * selects it); reductions are deterministic. */
 typedef struct {
   int32_t krylov_dim;      /* GMRES restart length m, 1..500 (default 30)          */
   int32_t max_restarts;    /* GMRES restarts per step, 0..1000 (default 0)          */
@@ -257,6 +258,12 @@ typedef struct {
                               of the local time steps, default), 1 solves the radial
                               line-implicit tridiagonal (Rusanov dissipation part of
                               D - J along each radial column)                        */
+  int32_t basis_fp32;      /* Krylov basis of crn_newton_krylov_step / crn_steady_solve:
+                              1 FP32 (orthogonalisation on the FP32 pipe, half the
+                              bytes; the basis vectors are rounded to FP32, which
+                              is far below a loose lin_rtol), 0 FP64, -1 FP32 when
+                              lin_rtol >= 1e-4 else FP64 (default -1).  The adjoint
+                              solve always uses FP64.                                */
 } crn_nk_options;
 
 typedef struct {

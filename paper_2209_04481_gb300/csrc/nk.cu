@@ -121,15 +121,72 @@ finish_kernel(const double* __restrict__ part, int nblk, int row0, double* __res
   if (threadIdx.x == 0) out[row] = sm[0];
 }
 
-// w += sum_t coef[t] V_t
+// w += sum_t coef[t] V_t (V FP64, or the FP32 basis into an FP64 w)
+template <class TV>
 __global__ void __launch_bounds__(NKB)
-maxpy_kernel(double* __restrict__ w, const double* __restrict__ V, int64_t n,
+maxpy_kernel(double* __restrict__ w, const TV* __restrict__ V, int64_t n,
              const double* __restrict__ coef, int cnt) {
   const int64_t stride = (int64_t)gridDim.x * NKB;
   for (int64_t e = (int64_t)blockIdx.x * NKB + threadIdx.x; e < n; e += stride) {
     double s = w[e];
-    for (int t = 0; t < cnt; ++t) s += coef[t] * V[(int64_t)t * n + e];
+    for (int t = 0; t < cnt; ++t) s += coef[t] * (double)V[(int64_t)t * n + e];
     w[e] = s;
+  }
+}
+
+// ---- FP32 Krylov basis: the orthogonalisation on the FP32 pipe (GB300 runs
+// FP64 FMAs at 1/64 of the FP32 rate, which bounds the FP64 multi-dot and
+// update); sums over a thread's elements in FP32, across threads in FP64
+
+// partial dots <Vf_(i0+t), wf>, t < cnt, into rows row_v + t; with ww <wf, wf>
+__global__ void __launch_bounds__(NKB)
+mdot32_kernel(const float* __restrict__ V, int64_t n, int i0, int cnt, const float* __restrict__ w,
+              double* __restrict__ part, int nblk, int row_v, int ww, int row_ww) {
+  float a[MD + 1];
+#pragma unroll
+  for (int t = 0; t <= MD; ++t) a[t] = 0.f;
+  const int64_t stride = (int64_t)nblk * NKB;
+#pragma unroll 2
+  for (int64_t e = (int64_t)blockIdx.x * NKB + threadIdx.x; e < n; e += stride) {
+    const float we = w[e];
+#pragma unroll
+    for (int t = 0; t < MD; ++t)
+      if (t < cnt) a[t] = fmaf(V[(int64_t)(i0 + t) * n + e], we, a[t]);
+    a[MD] = fmaf(we, we, a[MD]);
+  }
+  double b[MD];
+#pragma unroll
+  for (int t = 0; t < MD; ++t) b[t] = (double)a[t];
+  block_sum_rows<MD>(b, part, nblk, row_v, cnt);
+  if (ww) {
+    double c[1] = {(double)a[MD]};
+    __syncthreads();
+    block_sum_rows<1>(c, part, nblk, row_ww, 1);
+  }
+}
+
+// wf += sum_t coef[t] Vf_t in FP32
+__global__ void __launch_bounds__(NKB)
+maxpy32_kernel(float* __restrict__ w, const float* __restrict__ V, int64_t n,
+               const float* __restrict__ coef, int cnt) {
+  const int64_t stride = (int64_t)gridDim.x * NKB;
+  for (int64_t e = (int64_t)blockIdx.x * NKB + threadIdx.x; e < n; e += stride) {
+    float s = w[e];
+    for (int t = 0; t < cnt; ++t) s = fmaf(coef[t], V[(int64_t)t * n + e], s);
+    w[e] = s;
+  }
+}
+
+// y = (float)(a x); x FP64 (a new Arnoldi vector, a restart vector) or FP32
+template <class TX>
+__global__ void __launch_bounds__(NKB)
+to32_kernel(float* y, const TX* x, double a, int64_t n) {  // y may alias x when TX = float
+  const int64_t stride = (int64_t)gridDim.x * NKB;
+  if (sizeof(TX) == 4) {
+    const float af = (float)a;
+    for (int64_t e = (int64_t)blockIdx.x * NKB + threadIdx.x; e < n; e += stride) y[e] = af * (float)x[e];
+  } else {
+    for (int64_t e = (int64_t)blockIdx.x * NKB + threadIdx.x; e < n; e += stride) y[e] = (float)(a * (double)x[e]);
   }
 }
 
@@ -173,8 +230,9 @@ __device__ __forceinline__ double rcp_coarse(double x) {
 // two partial minima for the finite-difference step: over entries of
 // (|u| + s_v) / |z| into row `row`, and over cells of p / |dp_lin(z)| into
 // row `row` + 1 (dp_lin the linearised pressure change along z)
+template <class TV>
 __global__ void __launch_bounds__(NKB)
-precond_kernel(const double* __restrict__ v, const double* __restrict__ dtau, int64_t N,
+precond_kernel(const TV* __restrict__ v, const double* __restrict__ dtau, int64_t N,
                double* __restrict__ z, const double* __restrict__ U, const double* __restrict__ sumabs,
                double gm1, double* __restrict__ part, int nblk, int row, int want_min) {
   double m = INFINITY, mp = INFINITY;
@@ -195,7 +253,7 @@ precond_kernel(const double* __restrict__ v, const double* __restrict__ dtau, in
     double zz[NV];
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
-      zz[q] = d * v[q * N + c];
+      zz[q] = d * (double)v[q * N + c];
       if (dtau) z[q * N + c] = zz[q];
     }
     if (!want_min) continue;
@@ -253,9 +311,9 @@ perturb_kernel(const double* __restrict__ U, const double* __restrict__ z,
 
 // w = v - (R(U + eps z) - R(U)) / eps (forward difference, div = 1) or
 // w = v - (R(U + eps z) - R(U - eps z)) / (2 eps) (central difference, div = 2)
-template <class T>
+template <class T, class TV = double>
 __global__ void __launch_bounds__(NKB)
-jvp_combine_kernel(const double* __restrict__ v, const T* __restrict__ rp, const T* __restrict__ rb,
+jvp_combine_kernel(const TV* __restrict__ v, const T* __restrict__ rp, const T* __restrict__ rb,
                    const double* __restrict__ eps, double div, int64_t n, double* __restrict__ w,
                    const double* __restrict__ dinv = nullptr, const double* __restrict__ z = nullptr,
                    int64_t N = 1) {
@@ -263,7 +321,7 @@ jvp_combine_kernel(const double* __restrict__ v, const T* __restrict__ rp, const
   const int64_t stride = (int64_t)gridDim.x * NKB;
   for (int64_t e = (int64_t)blockIdx.x * NKB + threadIdx.x; e < n; e += stride) {
     // with dinv: the D z term of (D - J) z for a general right preconditioner
-    const double first = dinv ? dinv[e % N] * z[e] : (v ? v[e] : 0.0);
+    const double first = dinv ? dinv[e % N] * z[e] : (v ? (double)v[e] : 0.0);
     w[e] = first - ((double)rp[e] - (double)rb[e]) * ie;
   }
 }
@@ -482,21 +540,22 @@ line_factor_kernel(Shape sh, const double* __restrict__ lo, const double* __rest
 // thread per (variable, column): the nine right-hand sides share the factors,
 // and 9 n_theta n_phi threads keep every SM busy; the loads along r do not
 // depend on the recurrence and are issued ahead of it.
+template <class TV>
 __global__ void __launch_bounds__(NKB)
 line_solve_kernel(Shape sh, const double* __restrict__ lo, const double* __restrict__ cp,
-                  const double* __restrict__ im, const double* __restrict__ v, double* __restrict__ z) {
+                  const double* __restrict__ im, const TV* __restrict__ v, double* __restrict__ z) {
   const int64_t cs = (int64_t)sh.nt * sh.np, N = sh.ncell;
   const int64_t t = (int64_t)blockIdx.x * NKB + threadIdx.x;
   if (t >= NV * cs) return;
   const int64_t q = t / cs, col = t - q * cs;
-  const double* __restrict__ vq = v + q * N;
+  const TV* __restrict__ vq = v + q * N;
   double* __restrict__ zq = z + q * N;
-  double y = vq[col] * im[col];
+  double y = (double)vq[col] * im[col];
   zq[col] = y;
 #pragma unroll 4
   for (int k = 1; k < sh.nr; ++k) {
     const int64_t c = (int64_t)k * cs + col;
-    y = fma(-lo[c], y, vq[c]) * im[c];
+    y = fma(-lo[c], y, (double)vq[c]) * im[c];
     zq[c] = y;
   }
 #pragma unroll 4
@@ -530,6 +589,9 @@ struct NkWork {
   double* line = nullptr;  // 7N: radial line preconditioner (dinv, diag, lower, upper, the
                            //     factors c_k, upper of the transposed lines for the adjoint,
                            //     the inverse pivots 1/m_k)
+  float* Vf = nullptr;     // (m + 1) n: the FP32 Krylov basis (allocated on first use)
+  float* wf = nullptr;     // n: the FP32 Arnoldi vector
+  float* coef32 = nullptr; // m + 2 FP32 coefficients
   double* part = nullptr;  // rows x nblk partials
   double* out = nullptr;   // rows reduced values
   double* coef = nullptr;  // m + 2 coefficients
@@ -541,6 +603,7 @@ void nk_free(NkWork* w) {
   cudaFree(w->V); cudaFree(w->z); cudaFree(w->x); cudaFree(w->b); cudaFree(w->w);
   cudaFree(w->ut); cudaFree(w->rt); cudaFree(w->rb); cudaFree(w->rm); cudaFree(w->dtau);
   cudaFree(w->line);
+  cudaFree(w->Vf); cudaFree(w->wf); cudaFree(w->coef32);
   cudaFree(w->part); cudaFree(w->out); cudaFree(w->coef);
   cudaFreeHost(w->host);
   delete w;
@@ -563,6 +626,23 @@ struct Rows {
 };
 
 int report(int code, const std::string& msg) { return report_error(code, msg.c_str()); }
+
+// the FP32 Krylov basis of a workspace (allocated on first use)
+cudaError_t ensure_basis32(NkWork* w) {
+  if (w->Vf) return cudaSuccess;
+  cudaError_t e = cudaMalloc(&w->Vf, sizeof(float) * (size_t)(w->m + 1) * w->n);
+  if (e == cudaSuccess) e = cudaMalloc(&w->wf, sizeof(float) * w->n);
+  if (e == cudaSuccess) e = cudaMalloc(&w->coef32, sizeof(float) * (w->m + 2));
+  if (e != cudaSuccess) {
+    cudaFree(w->Vf); cudaFree(w->wf); cudaFree(w->coef32);
+    w->Vf = nullptr; w->wf = nullptr; w->coef32 = nullptr;
+  }
+  return e;
+}
+
+bool use_basis32(const crn_nk_options& o) {
+  return o.basis_fp32 == 1 || (o.basis_fp32 == -1 && o.lin_rtol >= 1e-4);
+}
 
 cudaError_t ensure_work(crn_grid* g, int m) {
   NkWork* w = g->nk;
@@ -646,7 +726,47 @@ struct Ctx {
     // c may be reused at once; stream order keeps coef intact for maxpy
     err = cudaMemcpyAsync(w->coef, c, sizeof(double) * cnt, cudaMemcpyHostToDevice, st);
     if (err != cudaSuccess) return;
-    maxpy_kernel<<<grid, NKB, 0, st>>>(y, w->V, n, w->coef, cnt);
+    maxpy_kernel<double><<<grid, NKB, 0, st>>>(y, w->V, n, w->coef, cnt);
+    ++launches;
+  }
+  // FP32 basis: h[t] = <Vf_t, vf> (rows 0..cnt-1), with ww also <vf, vf>
+  void dots32(int cnt, const float* v, bool ww) {
+    for (int i0 = 0; i0 < cnt || (i0 == 0 && ww); i0 += MD) {
+      const int c = std::min(MD, cnt - i0);
+      mdot32_kernel<<<w->nblk, NKB, 0, st>>>(w->Vf, n, i0, std::max(c, 0), v, w->part, w->nblk, i0,
+                                             (ww && i0 == 0) ? 1 : 0, rows.ww);
+      ++launches;
+      if (i0 + MD >= cnt) break;
+    }
+    if (cnt > 0) finish(0, cnt, 0);
+    if (ww) finish(rows.ww, 1, 0);
+  }
+  double norm32(const float* v) {
+    dots32(0, v, true);
+    fetch(rows.ww, 1);
+    return std::sqrt(std::max(w->host[rows.ww], 0.0));
+  }
+  // vf += sum_t c[t] Vf_t in FP32
+  void combine32(float* y, const double* c, int cnt) {
+    if (!ok() || cnt <= 0) return;
+    std::vector<float> cf(c, c + cnt);
+    // from pageable memory the copy returns once cf has been staged
+    err = cudaMemcpyAsync(w->coef32, cf.data(), sizeof(float) * cnt, cudaMemcpyHostToDevice, st);
+    if (err != cudaSuccess) return;
+    maxpy32_kernel<<<grid, NKB, 0, st>>>(y, w->Vf, n, w->coef32, cnt);
+    ++launches;
+  }
+  // x += sum_t c[t] Vf_t in FP64 (the solution update of a cycle)
+  void combine_x32(double* y, const double* c, int cnt) {
+    if (!ok() || cnt <= 0) return;
+    err = cudaMemcpyAsync(w->coef, c, sizeof(double) * cnt, cudaMemcpyHostToDevice, st);
+    if (err != cudaSuccess) return;
+    maxpy_kernel<float><<<grid, NKB, 0, st>>>(y, w->Vf, n, w->coef, cnt);
+    ++launches;
+  }
+  template <class TX>
+  void to32(float* y, const TX* x, double a) {
+    to32_kernel<TX><<<grid, NKB, 0, st>>>(y, x, a, n);
     ++launches;
   }
   void residual(const void* u, void* r) {
@@ -674,16 +794,24 @@ struct Ctx {
     ++launches;
   }
   // z = P^-1 v (radial lines, from the factors)
-  void line_solve(const double* v, double* z) {
+  template <class TV>
+  void line_solve(const TV* v, double* z) {
     const double* L = w->line;
     const unsigned nb = (unsigned)((NV * g->shape.nt * (int64_t)g->shape.np + NKB - 1) / NKB);
-    line_solve_kernel<<<nb, NKB, 0, st>>>(g->shape, mode == 1 ? L : L + 2 * N, L + 4 * N, L + 6 * N, v, z);
+    line_solve_kernel<TV><<<nb, NKB, 0, st>>>(g->shape, mode == 1 ? L : L + 2 * N, L + 4 * N, L + 6 * N, v, z);
     ++launches;
   }
 
-  void apply(const double* v, double* wout, const double* U, double b_rel, bool central) {
-    if (mode == 1) adjoint_op(v, wout);
-    else apply_op(v, wout, U, b_rel, central);
+  // v: a Krylov vector (FP64, or FP32 with the FP32 basis, forward mode only)
+  template <class TV>
+  void apply(const TV* v, double* wout, const double* U, double b_rel, bool central) {
+    if constexpr (sizeof(TV) == 8) {
+      if (mode == 1) {
+        adjoint_op(v, wout);
+        return;
+      }
+    }
+    apply_op(v, wout, U, b_rel, central);
   }
 
   // w_out = J^T (dtau . v) by the hand-written VJP of the residual; on FP32-bulk
@@ -692,8 +820,8 @@ struct Ctx {
     if (precond == 1) {
       line_solve(v, w->z);
     } else {
-      precond_kernel<<<w->nblk, NKB, 0, st>>>(v, w->dtau, N, w->z, nullptr, nullptr, 0.0, w->part, w->nblk,
-                                              rows.minr, 0);
+      precond_kernel<double><<<w->nblk, NKB, 0, st>>>(v, w->dtau, N, w->z, nullptr, nullptr, 0.0, w->part,
+                                                      w->nblk, rows.minr, 0);
       ++launches;
     }
     int nl = 0;
@@ -713,14 +841,15 @@ struct Ctx {
   }
 
   // w_out = v - J (dtau . v), J by a forward or central difference
-  void apply_op(const double* v, double* wout, const double* U, double b_rel, bool central) {
+  template <class TV>
+  void apply_op(const TV* v, double* wout, const double* U, double b_rel, bool central) {
     if (precond == 1) {
       line_solve(v, w->z);
-      precond_kernel<<<w->nblk, NKB, 0, st>>>(w->z, nullptr, N, w->z, U, w->out + rows.sumabs,
-                                              g->d.gamma - 1.0, w->part, w->nblk, rows.minr, 1);
+      precond_kernel<double><<<w->nblk, NKB, 0, st>>>(w->z, nullptr, N, w->z, U, w->out + rows.sumabs,
+                                                      g->d.gamma - 1.0, w->part, w->nblk, rows.minr, 1);
     } else {
-      precond_kernel<<<w->nblk, NKB, 0, st>>>(v, w->dtau, N, w->z, U, w->out + rows.sumabs,
-                                              g->d.gamma - 1.0, w->part, w->nblk, rows.minr, 1);
+      precond_kernel<TV><<<w->nblk, NKB, 0, st>>>(v, w->dtau, N, w->z, U, w->out + rows.sumabs,
+                                                  g->d.gamma - 1.0, w->part, w->nblk, rows.minr, 1);
     }
     ++launches;
     const double* dinv = precond == 1 ? w->line : nullptr;
@@ -739,8 +868,8 @@ struct Ctx {
         residual(w->ut, w->rb);
         base = (const double*)w->rb;
       }
-      jvp_combine_kernel<double><<<grid, NKB, 0, st>>>(v, (const double*)w->rt, base, e,
-                                                       central ? 2.0 : 1.0, n, wout, dinv, w->z, N);
+      jvp_combine_kernel<double, TV><<<grid, NKB, 0, st>>>(v, (const double*)w->rt, base, e,
+                                                           central ? 2.0 : 1.0, n, wout, dinv, w->z, N);
     } else {
       perturb_kernel<float><<<grid, NKB, 0, st>>>(U, w->z, e, 1.0, n, (float*)w->ut);
       ++launches;
@@ -752,8 +881,8 @@ struct Ctx {
         residual(w->ut, w->rm);
         base = (const float*)w->rm;
       }
-      jvp_combine_kernel<float><<<grid, NKB, 0, st>>>(v, (const float*)w->rt, base, e,
-                                                      central ? 2.0 : 1.0, n, wout, dinv, w->z, N);
+      jvp_combine_kernel<float, TV><<<grid, NKB, 0, st>>>(v, (const float*)w->rt, base, e,
+                                                          central ? 2.0 : 1.0, n, wout, dinv, w->z, N);
     }
     ++launches;
   }
@@ -778,8 +907,20 @@ double gmres(Ctx& c, const double* U, const crn_nk_options& o, double b_rel, dou
   const bool central = o.fd_central != 0;
   NkWork* w = c.w;
   const int m = o.krylov_dim;
+  // FP32 basis (forward mode): V_j in Vf, the new Arnoldi vector in wf after
+  // its FP64 product; FP64 basis: V_j and the new vector in V
+  const bool f32 = c.mode == 0 && use_basis32(o) && w->Vf;
   std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), y(m), h(m + 1), h2(m + 1);
   auto Hat = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
+  // V_0 = r / beta from an FP64 vector r
+  auto first = [&](const double* r, double beta) {
+    if (f32) {
+      c.to32(w->Vf, r, 1.0 / beta);
+    } else {
+      scale_kernel<<<c.grid, NKB, 0, c.st>>>(w->V, r, 1.0 / beta, c.n);
+      ++c.launches;
+    }
+  };
   cudaMemsetAsync(w->x, 0, sizeof(double) * c.n, c.st);
   iters = 0;
   double rel = 1.0;
@@ -789,8 +930,7 @@ double gmres(Ctx& c, const double* U, const crn_nk_options& o, double b_rel, dou
     double beta;
     if (cycle == 0) {
       beta = bnorm;
-      scale_kernel<<<c.grid, NKB, 0, c.st>>>(w->V, w->b, 1.0 / beta, c.n);
-      ++c.launches;
+      first(w->b, beta);
     } else {
       c.apply(w->x, w->w, U, b_rel, central);
       sub_kernel<<<c.grid, NKB, 0, c.st>>>(w->w, w->b, w->w, c.n);
@@ -799,41 +939,54 @@ double gmres(Ctx& c, const double* U, const crn_nk_options& o, double b_rel, dou
       if (!c.ok()) return rel;
       rel = beta / bnorm;
       if (rel <= o.lin_rtol || !(beta > 0.0)) return rel;
-      scale_kernel<<<c.grid, NKB, 0, c.st>>>(w->V, w->w, 1.0 / beta, c.n);
-      ++c.launches;
+      first(w->w, beta);
     }
     std::fill(gv.begin(), gv.end(), 0.0);
     gv[0] = beta;
     int jdone = 0;
     for (int j = 0; j < m; ++j) {
-      double* vj = w->V + (size_t)j * c.n;
-      double* vn = w->V + (size_t)(j + 1) * c.n;
-      c.apply(vj, vn, U, b_rel, central);
+      double* vn = w->V + (size_t)(j + 1) * c.n;  // FP64 basis: the new vector in place
+      float* vf = w->wf;                          // FP32 basis: the new vector
+      if (f32) {
+        c.apply(w->Vf + (size_t)j * c.n, w->w, U, b_rel, central);
+        c.to32(vf, w->w, 1.0);
+      } else {
+        c.apply(w->V + (size_t)j * c.n, vn, U, b_rel, central);
+      }
       ++iters;
+      auto dots = [&](bool ww) { if (f32) c.dots32(j + 1, vf, ww); else c.dots(j + 1, vn, ww); };
+      auto combine = [&](const double* coef) {
+        if (f32) c.combine32(vf, coef, j + 1); else c.combine(vn, coef, j + 1);
+      };
+      auto norm = [&]() { return f32 ? c.norm32(vf) : c.norm(vn); };
       // classical Gram-Schmidt, repeated once if the norm dropped by > 0.7
-      c.dots(j + 1, vn, true);
+      dots(true);
       c.fetch(0, j + 1);
       c.fetch(c.rows.ww, 1);
       if (!c.ok()) return rel;
       const double before = std::sqrt(std::max(w->host[c.rows.ww], 0.0));
       for (int t = 0; t <= j; ++t) h[t] = w->host[t];
       for (int t = 0; t <= j; ++t) h2[t] = -h[t];
-      c.combine(vn, h2.data(), j + 1);
-      double after = c.norm(vn);
+      combine(h2.data());
+      double after = norm();
       if (after < 0.7 * before) {
-        c.dots(j + 1, vn, false);
+        dots(false);
         c.fetch(0, j + 1);
         if (!c.ok()) return rel;
         for (int t = 0; t <= j; ++t) { h2[t] = -w->host[t]; h[t] += w->host[t]; }
-        c.combine(vn, h2.data(), j + 1);
-        after = c.norm(vn);
+        combine(h2.data());
+        after = norm();
       }
       if (!c.ok()) return rel;
       for (int t = 0; t <= j; ++t) Hat(t, j) = h[t];
       Hat(j + 1, j) = after;
       if (after > 0.0) {
-        scale_kernel<<<c.grid, NKB, 0, c.st>>>(vn, vn, 1.0 / after, c.n);
-        ++c.launches;
+        if (f32) {
+          c.to32(w->Vf + (size_t)(j + 1) * c.n, vf, 1.0 / after);
+        } else {
+          scale_kernel<<<c.grid, NKB, 0, c.st>>>(vn, vn, 1.0 / after, c.n);
+          ++c.launches;
+        }
       }
       // Givens rotations on column j
       for (int t = 0; t < j; ++t) {
@@ -859,7 +1012,8 @@ double gmres(Ctx& c, const double* U, const crn_nk_options& o, double b_rel, dou
       for (int q = t + 1; q < jdone; ++q) s -= Hat(t, q) * y[q];
       y[t] = Hat(t, t) != 0.0 ? s / Hat(t, t) : 0.0;
     }
-    c.combine(w->x, y.data(), jdone);
+    if (f32) c.combine_x32(w->x, y.data(), jdone);
+    else c.combine(w->x, y.data(), jdone);
     if (rel <= o.lin_rtol) break;
   }
   return rel;
@@ -891,6 +1045,7 @@ int nk_step(crn_grid* g, double* U, double cfl, const crn_nk_options& o, crn_nk_
             cudaStream_t st, int& launches, double stop_below, bool& stopped) {
   stopped = false;
   cudaError_t e = ensure_work(g, o.krylov_dim);
+  if (e == cudaSuccess && use_basis32(o)) e = ensure_basis32(g->nk);
   if (e != cudaSuccess) return report(CRN_E_CUDA, std::string("Newton-Krylov workspace: ") + cudaGetErrorString(e));
   Ctx c(g, st);
   c.precond = o.precond;
@@ -951,7 +1106,7 @@ int nk_step(crn_grid* g, double* U, double cfl, const crn_nk_options& o, crn_nk_
   if (o.precond == 1) {
     c.line_solve(w->x, w->z);
   } else {
-    precond_kernel<<<w->nblk, NKB, 0, st>>>(w->x, w->dtau, c.N, w->z, U, w->out + c.rows.sumabs, gm1,
+    precond_kernel<double><<<w->nblk, NKB, 0, st>>>(w->x, w->dtau, c.N, w->z, U, w->out + c.rows.sumabs, gm1,
                                             w->part, w->nblk, c.rows.minr, 0);
     ++c.launches;
   }
@@ -1008,6 +1163,7 @@ int check_nk_options(const crn_nk_options& o) {
   if (!std::isfinite(o.max_rel_change)) return report(CRN_E_ARG, "max_rel_change must be finite");
   if (o.fd_central != 0 && o.fd_central != 1) return report(CRN_E_ARG, "fd_central must be 0 or 1");
   if (o.precond != 0 && o.precond != 1) return report(CRN_E_ARG, "precond must be 0 or 1");
+  if (o.basis_fp32 < -1 || o.basis_fp32 > 1) return report(CRN_E_ARG, "basis_fp32 must be -1, 0 or 1");
   return CRN_OK;
 }
 
@@ -1071,7 +1227,7 @@ int adjoint_solve(crn_grid* g, const double* U, const double* gbar, double* lamb
   if (o.precond == 1) {
     c.line_solve(w->x, w->z);
   } else {
-    precond_kernel<<<w->nblk, NKB, 0, st>>>(w->x, w->dtau, c.N, w->z, nullptr, nullptr, 0.0, w->part, w->nblk,
+    precond_kernel<double><<<w->nblk, NKB, 0, st>>>(w->x, w->dtau, c.N, w->z, nullptr, nullptr, 0.0, w->part, w->nblk,
                                             c.rows.minr, 0);
     ++c.launches;
   }
@@ -1119,6 +1275,7 @@ int crn_nk_options_default(crn_nk_options* o) {
   o->fd_rel = 0.0;
   o->max_rel_change = 0.3;
   o->fd_central = 1;
+  o->basis_fp32 = -1;
   return CRN_OK;
 }
 

@@ -176,3 +176,33 @@ def test_steady_solve_with_the_radial_line_preconditioner():
     r0 = np.linalg.norm(oracle.residual(og, U, Br)["R"])
     r1 = np.linalg.norm(oracle.residual(og, U64.cpu().numpy(), Br)["R"])
     assert r1 <= 2e-6 * r0
+
+
+@pytest.mark.parametrize("precond", [0, 1])
+def test_fp32_krylov_basis_reaches_the_same_steady_state(precond):
+    """The FP32 Krylov basis (basis_fp32 = 1; the default at lin_rtol 1e-3)
+    takes about as many steps as the FP64 basis to the same steady state."""
+    shape = (32, 16, 32)
+    out = {}
+    for basis in (0, 1):
+        g, U, Br, og = setup(shape, "low_e_wp", "fp64", dipole_only=True)
+        U64 = torch.from_numpy(U).cuda()
+        stats, hist = g.steady_solve(U64, max_steps=300, tol_drop=1e-6,
+                                     nk=dict(precond=precond, basis_fp32=basis))
+        g.sync_status()
+        assert stats["converged"] == 1, (basis, stats, hist[-5:])
+        out[basis] = (stats, U64.cpu().numpy())
+    (s0, U0), (s1, U1) = out[0], out[1]
+    assert abs(s1["steps"] - s0["steps"]) <= max(3, s0["steps"] // 10), (s0, s1)
+    err = per_var_err(U1, U0)
+    assert np.all(err < 1e-4), err
+    r0 = np.linalg.norm(oracle.residual(og, U, Br)["R"])
+    r1 = np.linalg.norm(oracle.residual(og, U1, Br)["R"])
+    assert r1 <= 2e-6 * r0
+
+
+def test_krylov_basis_option_is_checked():
+    import paper_2209_04481_gb300 as pg
+    g, U, Br, og = setup((6, 8, 16), "low_e", "fp64", seed=5)
+    with pytest.raises(pg.CoronaError, match="basis_fp32"):
+        g.newton_krylov_step(torch.from_numpy(U).cuda(), 2.0, basis_fp32=2)

@@ -62,7 +62,7 @@ def test_newton_krylov_option_defaults(lib):
     assert lib.crn_steady_options_default(ctypes.byref(o)) == 0
     assert (o.cfl0, o.cfl_max, o.cfl_double_every, o.max_steps, o.tol_drop) == (2.0, 128.0, 10, 500, 1e-6)
     assert (o.nk.krylov_dim, o.nk.max_restarts, o.nk.lin_rtol, o.nk.fd_rel, o.nk.max_rel_change,
-            o.nk.fd_central) == (30, 0, 1e-3, 0.0, 0.3, 1)
+            o.nk.fd_central, o.nk.precond, o.nk.basis_fp32) == (30, 0, 1e-3, 0.0, 0.3, 1, 0, -1)
     n = pg.NkOptions()
     assert lib.crn_nk_options_default(ctypes.byref(n)) == 0
     assert n.krylov_dim == 30 and n.lin_rtol == 1e-3
