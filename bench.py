@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--only-headline", nargs="?", const="fp32", choices=["fp32", "fp64"], default=None,
                     help="time the residual in this precision only (for profiler captures); skips "
                          "e2e, pseudo-time, VJP, Newton-Krylov and ensemble measurements")
+    ap.add_argument("--only-newton-krylov", action="store_true",
+                    help="run the 96x48x96 Newton-Krylov solve only, for at most --steps "
+                         "pseudo-time steps (for profiler captures)")
     ap.add_argument("--only-pseudo-time", action="store_true",
                     help="time the FP32-bulk residual and then the explicit pseudo-time step only "
                          "(for profiler captures of the update kernel)")
@@ -290,6 +293,16 @@ def run_gb300(args):
     dist = init_dist(world, "nccl")
     pg.load_library()
 
+    if args.only_newton_krylov:
+        stream = torch.cuda.Stream(device)
+        nk = run_nk(torch, pg, ci, device, stream, only="shell96_fp64_minmod", steps_cap=args.steps)
+        if rank == 0:
+            print(json.dumps({"newton_krylov": nk, "note": "Newton-Krylov solve only (profiling run)"}),
+                  flush=True)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
     # independent replica per rank: its own magnetogram seed
     U0, info = ci.background(*SHAPE)
     Br = ci.magnetogram(SHAPE[1], SHAPE[2], seed=2209 + rank)
@@ -475,20 +488,26 @@ def run_gb300(args):
         dist.destroy_process_group()
 
 
-def run_nk(torch, pg, ci, device, stream):
+def run_nk(torch, pg, ci, device, stream, only=None, steps_cap=None):
     """Newton-Krylov steady solves (backward-Euler pseudo-time, CFL 2 doubling
     every 10 steps to 128, GMRES(30) to 1e-3, central-difference JVPs) from the
     Parker wind + dipole start with the low-E inner boundary of prescribed
-    outflow magnitude; wall-clock time around the host-driven solve."""
+    outflow magnitude; wall-clock time around the host-driven solve.  `only`
+    names the one run to make, `steps_cap` bounds its pseudo-time steps."""
     vr = 1935.07 / ci.V_REF
     out = {"note": "dipole start (the strong-field l<=15 start drains a base cell to vacuum under "
-                   "any pseudo-time schedule); inner_bc low_e_wp; wall-clock seconds"}
+                   "any pseudo-time schedule); inner_bc low_e_wp; wall-clock seconds; Krylov basis "
+                   "FP32 (the default at lin_rtol 1e-3), adjoint FP64"}
     # (name, shape, precision, limiter, drop, max steps, CFL cap, Newton-Krylov options)
     runs = (("shell32_fp64", (32, 16, 32), "fp64", "vanalbada", 1e-6, 300, 128.0, {}),
             # SURVEY config 4: minmod, CFL up to 1024, radial line preconditioner, GMRES(60)
             ("shell96_fp64_minmod", (96, 48, 96), "fp64", "minmod", 1e-6, 300, 1024.0,
              {"precond": 1, "krylov_dim": 60}))
     for name, shape, precision, limiter, tol, max_steps, cfl_max, nkopt in runs:
+        if only is not None and name != only:
+            continue
+        if steps_cap is not None:
+            max_steps = min(max_steps, steps_cap)
         U, info = ci.background(*shape)
         Br = ci.magnetogram(shape[1], shape[2], dipole_only=True)
         g = pg.Grid(*shape, precision=precision, limiter=limiter, p_b=info["p_b"], inner_bc="low_e_wp",

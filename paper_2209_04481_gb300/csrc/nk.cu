@@ -37,6 +37,7 @@
 #include <vector>
 
 #include "corona_internal.h"
+#include "fp_bits.cuh"
 
 namespace crn {
 
@@ -540,6 +541,11 @@ line_factor_kernel(Shape sh, const double* __restrict__ lo, const double* __rest
 // thread per (variable, column): the nine right-hand sides share the factors,
 // and 9 n_theta n_phi threads keep every SM busy; the loads along r do not
 // depend on the recurrence and are issued ahead of it.
+// an FP32 Krylov vector widens on the integer pipe (exact): the FP64 pipe,
+// which also runs the conversion instruction, carries the recurrence
+__device__ __forceinline__ double as_double(float x) { return widen_f32(x); }
+__device__ __forceinline__ double as_double(double x) { return x; }
+
 template <class TV>
 __global__ void __launch_bounds__(NKB)
 line_solve_kernel(Shape sh, const double* __restrict__ lo, const double* __restrict__ cp,
@@ -550,12 +556,12 @@ line_solve_kernel(Shape sh, const double* __restrict__ lo, const double* __restr
   const int64_t q = t / cs, col = t - q * cs;
   const TV* __restrict__ vq = v + q * N;
   double* __restrict__ zq = z + q * N;
-  double y = (double)vq[col] * im[col];
+  double y = as_double(vq[col]) * im[col];
   zq[col] = y;
 #pragma unroll 4
   for (int k = 1; k < sh.nr; ++k) {
     const int64_t c = (int64_t)k * cs + col;
-    y = fma(-lo[c], y, (double)vq[c]) * im[c];
+    y = fma(-lo[c], y, as_double(vq[c])) * im[c];
     zq[c] = y;
   }
 #pragma unroll 4
