@@ -225,8 +225,19 @@ __device__ __forceinline__ T limited_slope(T a, T b, T eps) {
   if (LIM == 0) {  // unlimited central
     return (T)0.5 * (a + b);
   } else if (LIM == 1) {  // minmod
-    const T m = fabs(a) < fabs(b) ? a : b;
-    return a * b > (T)0 ? m : (T)0;
+    if constexpr (sizeof(T) == 8) {
+      // on the integer pipe (FP64 compares and products use the slow FP64
+      // pipe): a b > 0 iff both are nonzero with equal sign bits, and the
+      // magnitudes of non-negative doubles order as their bit patterns
+      const unsigned long long ba = (unsigned long long)__double_as_longlong(a);
+      const unsigned long long bb = (unsigned long long)__double_as_longlong(b);
+      const unsigned long long ma = ba & 0x7fffffffffffffffull, mb = bb & 0x7fffffffffffffffull;
+      const bool pos = ma != 0ull && mb != 0ull && ((ba ^ bb) >> 63) == 0ull;
+      return pos ? (ma < mb ? a : b) : (T)0;
+    } else {
+      const T m = fabs(a) < fabs(b) ? a : b;
+      return a * b > (T)0 ? m : (T)0;
+    }
   } else {  // van Albada, smooth form; explicit FMAs so that every kernel
             // inlining this rounds it the same way
     const T num = fmat(a, fmat(b, b, eps), b * fmat(a, a, eps));
