@@ -502,7 +502,10 @@ def run_nk(torch, pg, ci, device, stream, only=None, steps_cap=None):
     runs = (("shell32_fp64", (32, 16, 32), "fp64", "vanalbada", 1e-6, 300, 128.0, {}),
             # SURVEY config 4: minmod, CFL up to 1024, radial line preconditioner, GMRES(60)
             ("shell96_fp64_minmod", (96, 48, 96), "fp64", "minmod", 1e-6, 300, 1024.0,
-             {"precond": 1, "krylov_dim": 60}))
+             {"precond": 1, "krylov_dim": 60}),
+            # the same solve with forward-difference JVPs: one residual per Krylov step
+            ("shell96_fp64_minmod_forward_fd", (96, 48, 96), "fp64", "minmod", 1e-6, 300, 1024.0,
+             {"precond": 1, "krylov_dim": 60, "fd_central": 0}))
     for name, shape, precision, limiter, tol, max_steps, cfl_max, nkopt in runs:
         if only is not None and name != only:
             continue
