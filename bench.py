@@ -500,7 +500,7 @@ def run_nk(torch, pg, ci, device, stream, only=None, steps_cap=None):
                    "FP32 (the default at lin_rtol 1e-3), adjoint FP64"}
     # (name, shape, precision, limiter, drop, max steps, CFL cap, Newton-Krylov options)
     runs = (("shell32_fp64", (32, 16, 32), "fp64", "vanalbada", 1e-6, 300, 128.0, {}),
-            # SURVEY config 4: minmod, CFL up to 1024, radial line preconditioner, GMRES(60)
+            # 96x48x96: minmod, CFL up to 1024, radial line preconditioner, GMRES(60)
             ("shell96_fp64_minmod", (96, 48, 96), "fp64", "minmod", 1e-6, 300, 1024.0,
              {"precond": 1, "krylov_dim": 60}),
             # the same solve with forward-difference JVPs: one residual per Krylov step
