@@ -25,9 +25,10 @@
 // U + alpha dU would have rho <= 0 or p <= 0.  The CFL law of Sect. 4.1
 // (start at 2, double every few steps, up to 128) drives crn_steady_solve.
 //
-// Every vector operation is an FP64 kernel of this file; reductions go through
-// per-block partials summed in a fixed order, so a solve is bitwise
-// reproducible.  The host runs the GMRES recurrences (Hessenberg, Givens) and
+// Every vector operation is a kernel of this file, in FP64 except the
+// Gram-Schmidt dots and updates of an FP32 Krylov basis (basis_fp32);
+// reductions go through per-block partials summed in a fixed order, so a
+// solve is bitwise reproducible.  The host runs the GMRES recurrences (Hessenberg, Givens) and
 // synchronises the stream once or twice per Krylov step to read the dots.
 #include <algorithm>
 #include <cmath>
