@@ -57,6 +57,10 @@ def parse():
     ap.add_argument("--only-newton-krylov", action="store_true",
                     help="run the 96x48x96 Newton-Krylov solve only, for at most --steps "
                          "pseudo-time steps (for profiler captures)")
+    ap.add_argument("--only-vjp", action="store_true",
+                    help="time the residual VJP only (for profiler captures)")
+    ap.add_argument("--only-ensemble", action="store_true",
+                    help="run the 32-shell ensemble measurement only (for profiler captures)")
     ap.add_argument("--only-pseudo-time", action="store_true",
                     help="time the FP32-bulk residual and then the explicit pseudo-time step only "
                          "(for profiler captures of the update kernel)")
@@ -293,6 +297,16 @@ def run_gb300(args):
     dist = init_dist(world, "nccl")
     pg.load_library()
 
+    if args.only_vjp or args.only_ensemble:
+        import numpy as np
+        stream = torch.cuda.Stream(device)
+        res = ({"vjp": run_vjp(torch, np, pg, ci, device, stream)} if args.only_vjp
+               else {"ensemble": run_ensemble(torch, pg, ci, device, stream, nsteps=min(args.steps, 200))})
+        if rank == 0:
+            print(json.dumps(dict(res, note="profiling run")), flush=True)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
     if args.only_newton_krylov:
         stream = torch.cuda.Stream(device)
         nk = run_nk(torch, pg, ci, device, stream, only="shell96_fp64_minmod", steps_cap=args.steps)
@@ -418,36 +432,7 @@ def run_gb300(args):
     del graph
     g64.close()
 
-    # ---- residual VJP on the 64 x 32 x 64 perturbed shell (adjoint workload)
-    vjp = {}
-    wv = ci.workload("shell64")
-    nv = int(np.prod(wv["shape"]))
-    for precision in ("fp64", "fp32"):
-        gv = pg.Grid(*wv["shape"], precision=precision, p_b=wv["p_b"])
-        gv.set_inner_boundary(torch.from_numpy(wv["Br"]).to(device))
-        dtv = torch.float64 if precision == "fp64" else torch.float32
-        Uv = torch.from_numpy(wv["U"]).to(device, dtv)
-        Rbv = torch.from_numpy(ci.cotangent(wv["U"].shape, seed=4)).to(device, dtv)
-        Ubv = torch.empty_like(Uv)
-        Brbv = torch.empty(wv["shape"][1:], dtype=torch.float64, device=device)
-        with torch.cuda.stream(stream):
-            for _ in range(3):
-                gv.residual_vjp(Uv, Rbv, Ubv, Brbv, stream=stream)
-        stream.synchronize()
-        nrep = 20 if precision == "fp64" else 50
-        v0 = torch.cuda.Event(enable_timing=True)
-        v1 = torch.cuda.Event(enable_timing=True)
-        with torch.cuda.stream(stream):
-            v0.record(stream)
-            for _ in range(nrep):
-                gv.residual_vjp(Uv, Rbv, Ubv, Brbv, stream=stream)
-            v1.record(stream)
-        torch.cuda.synchronize(device)
-        ms = v0.elapsed_time(v1) / nrep
-        vjp[precision] = {"ms_per_vjp": ms, "cells_per_s": nv / (ms / 1e3),
-                          "launches_per_vjp": gv.last_launch_count}
-        gv.close()
-    vjp["workload"] = "64x32x64 shell, dipole, 1% perturbation (seed 3), N(0,1) cotangent (seed 4)"
+    vjp = run_vjp(torch, np, pg, ci, device, stream)
 
     nk = run_nk(torch, pg, ci, device, stream)
     ens = run_ensemble(torch, pg, ci, device, stream)
@@ -486,6 +471,41 @@ def run_gb300(args):
         print(json.dumps(result), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def run_vjp(torch, np, pg, ci, device, stream):
+    """Residual VJP on the 64 x 32 x 64 perturbed shell (adjoint workload),
+    FP64 and FP32 bulk, timed with CUDA events over repeated calls."""
+    vjp = {}
+    wv = ci.workload("shell64")
+    nv = int(np.prod(wv["shape"]))
+    for precision in ("fp64", "fp32"):
+        gv = pg.Grid(*wv["shape"], precision=precision, p_b=wv["p_b"])
+        gv.set_inner_boundary(torch.from_numpy(wv["Br"]).to(device))
+        dtv = torch.float64 if precision == "fp64" else torch.float32
+        Uv = torch.from_numpy(wv["U"]).to(device, dtv)
+        Rbv = torch.from_numpy(ci.cotangent(wv["U"].shape, seed=4)).to(device, dtv)
+        Ubv = torch.empty_like(Uv)
+        Brbv = torch.empty(wv["shape"][1:], dtype=torch.float64, device=device)
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                gv.residual_vjp(Uv, Rbv, Ubv, Brbv, stream=stream)
+        stream.synchronize()
+        nrep = 20 if precision == "fp64" else 50
+        v0 = torch.cuda.Event(enable_timing=True)
+        v1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            v0.record(stream)
+            for _ in range(nrep):
+                gv.residual_vjp(Uv, Rbv, Ubv, Brbv, stream=stream)
+            v1.record(stream)
+        torch.cuda.synchronize(device)
+        ms = v0.elapsed_time(v1) / nrep
+        vjp[precision] = {"ms_per_vjp": ms, "cells_per_s": nv / (ms / 1e3),
+                          "launches_per_vjp": gv.last_launch_count}
+        gv.close()
+    vjp["workload"] = "64x32x64 shell, dipole, 1% perturbation (seed 3), N(0,1) cotangent (seed 4)"
+    return vjp
 
 
 def run_nk(torch, pg, ci, device, stream, only=None, steps_cap=None):

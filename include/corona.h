@@ -161,7 +161,8 @@ int crn_residual(crn_grid* g, const void* U_dev, void* R_dev, double* norms9_dev
  * recomputed, not stored.  Non-smooth points: max passes the derivative to
  * its first argument on a tie, d|x|/dx = +1 at 0.  The first call on a grid
  * allocates its scratch (36 values of the grid's type per face, about 108 per
- * cell): make it before any stream capture.  Asynchronous, 4 launches. */
+ * cell): make it before any stream capture.  Asynchronous, 2 launches (3 on
+ * CRN_FP64 grids, which recover the primitives once first). */
 int crn_residual_vjp(crn_grid* g, const void* U_dev, const void* Rbar_dev, void* Ubar_dev,
                      double* Brbar_dev, void* stream);
 

@@ -379,20 +379,29 @@ __device__ __forceinline__ void zero_contrib(T* buf, int64_t nf, int64_t f) {
   for (int q = 0; q < 4 * NV; ++q) buf[(int64_t)q * nf + f] = (T)0;
 }
 
-// axis: 0 = r, 1 = theta, 2 = phi
+// One launch over the faces of all three axes (r faces, then theta, then
+// phi): a thread per face, so that small grids still fill the GPU with
+// several waves of these long threads.
 template <class T, int LIM>
 __global__ void __launch_bounds__(128)
 vjp_faces(Shape sh, Geo<T> g, Phys<T> ph, const double* __restrict__ Br, const T* __restrict__ U,
-          const T* __restrict__ Rb, VjpBufs<T> out, int axis) {
+          const T* __restrict__ Rb, VjpBufs<T> out) {
   const int nr = sh.nr, nt = sh.nt, np = sh.np;
   const int64_t cs = (int64_t)nt * np, N = sh.ncell;
-  int64_t nf;
-  T* buf;
-  if (axis == 0) { nf = (int64_t)(nr + 1) * cs; buf = out.cr; }
-  else if (axis == 1) { nf = (int64_t)nr * (nt + 1) * np; buf = out.ct; }
-  else { nf = (int64_t)nr * cs; buf = out.cp; }
-  const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= nf) return;
+  const int64_t nf0 = (int64_t)(nr + 1) * cs, nf1 = (int64_t)nr * (nt + 1) * np, nf2 = (int64_t)nr * cs;
+  int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int axis = 0;  // 0 = r, 1 = theta, 2 = phi
+  int64_t nf = nf0;
+  T* buf = out.cr;
+  if (f >= nf0) {
+    f -= nf0;
+    axis = 1; nf = nf1; buf = out.ct;
+    if (f >= nf1) {
+      f -= nf1;
+      axis = 2; nf = nf2; buf = out.cp;
+      if (f >= nf2) return;
+    }
+  }
   const T one = (T)1, half = (T)0.5;
   int k, j, i, a;           // a: face index along the axis; (k, j, i) the other two + dummy
   T nx, ny, nz, area;

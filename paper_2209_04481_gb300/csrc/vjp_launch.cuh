@@ -34,15 +34,12 @@ cudaError_t vjp_lim(crn_grid* g, const T* U, const T* Rb, T* Ub, double* Brb, cu
   // recovery inside the face pass is cheaper than one more pass over memory
   b.W = sizeof(T) == 8 ? b.cp + (size_t)4 * NV * sh.nr * cs : nullptr;
   if (b.W) vjp_prims<T><<<(unsigned)((sh.ncell + 255) / 256), 256, 0, st>>>(sh, vphys<T>(g), U, b.W);
-  const int64_t nf[3] = {(int64_t)(sh.nr + 1) * (int64_t)cs, (int64_t)sh.nr * (sh.nt + 1) * sh.np,
-                         (int64_t)sh.nr * (int64_t)cs};
-  for (int axis = 0; axis < 3; ++axis) {
-    const unsigned nb = (unsigned)((nf[axis] + 127) / 128);
-    vjp_faces<T, LIM><<<nb, 128, 0, st>>>(sh, vgeo<T>(g), vphys<T>(g), g->br, U, Rb, b, axis);
-  }
+  const int64_t nf = (int64_t)(sh.nr + 1) * (int64_t)cs + (int64_t)sh.nr * (sh.nt + 1) * sh.np +
+                     (int64_t)sh.nr * (int64_t)cs;
+  vjp_faces<T, LIM><<<(unsigned)((nf + 127) / 128), 128, 0, st>>>(sh, vgeo<T>(g), vphys<T>(g), g->br, U, Rb, b);
   const unsigned nbc = (unsigned)((sh.ncell + 127) / 128);
   vjp_cells<T><<<nbc, 128, 0, st>>>(sh, vgeo<T>(g), vphys<T>(g), g->br, U, Rb, b, Ub, Brb);
-  *nl = b.W ? 5 : 4;
+  *nl = b.W ? 3 : 2;
   return cudaGetLastError();
 }
 
