@@ -238,9 +238,10 @@ __device__ __forceinline__ T limited_slope(T a, T b, T eps) {
       const T m = fabs(a) < fabs(b) ? a : b;
       return a * b > (T)0 ? m : (T)0;
     }
-  } else {  // van Albada, smooth form; explicit FMAs so that every kernel
-            // inlining this rounds it the same way
-    const T num = fmat(a, fmat(b, b, eps), b * fmat(a, a, eps));
+  } else {  // van Albada, smooth form: a (b^2 + eps) + b (a^2 + eps) is
+            // (a + b)(a b + eps), one operation fewer; explicit FMAs so that
+            // every kernel inlining this rounds it the same way
+    const T num = (a + b) * fmat(a, b, eps);
     const T den = fmat(a, a, fmat(b, b, (T)2 * eps));
     return num * frcp(den);
   }
@@ -254,9 +255,9 @@ __device__ __forceinline__ T limited_slope(T a, T b, T eps) {
 template <int LIM, class T>
 __device__ __forceinline__ void limited_slope2(T a1, T b1, T a2, T b2, T eps, T& s1, T& s2) {
   if (LIM == 2 && sizeof(T) == 8) {
-    const T n1 = fmat(a1, fmat(b1, b1, eps), b1 * fmat(a1, a1, eps));
+    const T n1 = (a1 + b1) * fmat(a1, b1, eps);
     const T d1 = fmat(a1, a1, fmat(b1, b1, (T)2 * eps));
-    const T n2 = fmat(a2, fmat(b2, b2, eps), b2 * fmat(a2, a2, eps));
+    const T n2 = (a2 + b2) * fmat(a2, b2, eps);
     const T d2 = fmat(a2, a2, fmat(b2, b2, (T)2 * eps));
     const T inv = frcp(d1 * d2);
     s1 = n1 * (inv * d2);
