@@ -194,6 +194,58 @@ def test_flux_rotation_invariance_and_dissipation():
                                    rtol=1e-12, atol=1e-12)
 
 
+def test_flux_energy_is_enthalpy_plus_poynting():
+    """The consistent energy flux of ideal MHD, written through the electric
+    field E = -V x B of Sect. 2.2, is the kinetic plus enthalpy flux plus the
+    Poynting flux: F_E = (rho V^2/2 + gamma p/(gamma-1)) u_n + (E x B).n.
+    States with V neither along nor across B make the magnetic work term
+    -B_n (V.B) of the flux visible (it vanishes in the Euler, magnetostatic
+    and V || B limits); psi does not enter the energy flux."""
+    rng = np.random.default_rng(23)
+    for _ in range(20):
+        w = np.array([0.5 + rng.random(), *rng.standard_normal(3), *rng.standard_normal(3),
+                      0.2 + rng.random(), 0.3 * rng.standard_normal()])
+        n = rng.standard_normal(3)
+        n /= np.linalg.norm(n)
+        F, _ = oracle.flux(w, w, n, gamma=GAM, c_h=1.0)
+        V, B, rho, p = w[1:4], w[4:7], w[0], w[7]
+        efield = -np.cross(V, B)
+        poynting = np.cross(efield, B) @ n
+        expect = (0.5 * rho * V @ V + GAM * p / (GAM - 1.0)) * (V @ n) + poynting
+        scale = (0.5 * rho * V @ V + GAM * p / (GAM - 1.0) + B @ B) * np.linalg.norm(V)
+        assert abs(F[7] - expect) <= 1e-13 * scale, (F[7], expect)
+
+
+def test_free_stream_gravity_source():
+    """A uniform state with V parallel to B under gravity: every face flux is
+    the same on both sides and the exact face vectors close, so the residual
+    is the source of Sect. 2.2 alone, cell by cell: rho g in the momentum,
+    rho g.V in the energy, with g = -g0 rhat / r^2 at the cell centre."""
+    g0 = ci.G0_SOLAR
+    g = sphere(6, 8, 12, limiter="vanalbada", g0=g0, outer_rho_exp=0.0, outer_br_exp=0.0)
+    bhat = np.array([0.3, -0.5, 0.81])
+    bhat /= np.linalg.norm(bhat)
+    rho, p = 0.8, 0.3
+    V, B = 0.4 * bhat, 1.1 * bhat
+    w = np.array([rho, *V, *B, p, 0.0])
+    U = np.broadcast_to(cons(w, g.gamma)[:, None, None, None], (9,) + g.shape).copy()
+    rc, tc, pc = centres(g)
+    Rr, T, P = np.meshgrid(rc, tc, pc, indexing="ij")
+    er = np.stack([np.sin(T) * np.cos(P), np.sin(T) * np.sin(P), np.cos(T)])
+    grav = -g0 * er / Rr ** 2
+    Br = np.einsum("c,cjk->jk", B, rhat_grid(g))
+    g.rho_b, g.p_b = rho, p
+    out = oracle.residual(g, U, Br, want_scale=True)
+    R = out["R"]
+    tol = 1e-13 * out["scale"].max(axis=(1, 2, 3))
+    np.testing.assert_array_less(np.abs(R[1:4] - rho * grav).max(axis=(1, 2, 3)), tol[1:4])
+    work = rho * np.einsum("c,ckji->kji", V, grav)
+    assert np.abs(work).min() > 1e-3 * np.abs(work).max() or np.abs(work).max() > 1e-2
+    assert np.abs(R[7] - work).max() < tol[7], np.abs(R[7] - work).max()
+    for v in (0, 4, 5, 6, 8):
+        assert np.abs(R[v]).max() < tol[v] + 1e-15
+
+
 # ---------------------------------------------------------------------------
 # full residual on the shell
 # ---------------------------------------------------------------------------
@@ -463,6 +515,59 @@ def test_alfven_wave_convergence(limiter, min_order):
         errs.append(np.mean(np.abs(R[4:7] - exact[4:7])) + np.mean(np.abs(R[1:4] - exact[1:4])))
     orders = [math.log2(errs[i] / errs[i + 1]) for i in range(3)]
     assert orders[-1] > min_order, (errs, orders)
+
+
+def _boosted_alfven_state(g, u0, amp=0.1, rho=1.0, p=0.1, b0=1.0):
+    """The circularly polarised Alfven wave seen from a frame moving at -u0:
+    ideal MHD is Galilean invariant, so W(x - u0 t, t) with V + u0 is again an
+    exact solution, and its time derivative is the wave's own minus
+    (u0 . grad) W.  With u0 across k, V.B varies along k."""
+    W, dW = _alfven_state(g, amp=amp, rho=rho, p=p, b0=b0)
+    n0, n1, _ = g.shape
+    x = (np.arange(n0) + 0.5) / n0
+    y = (np.arange(n1) + 0.5) / n1
+    X, Y = np.meshgrid(x, y, indexing="ij")
+    kk = np.array([1.0, 1.0, 0.0]) / math.sqrt(2.0)
+    e1 = np.array([-1.0, 1.0, 0.0]) / math.sqrt(2.0)
+    e2 = np.array([0.0, 0.0, 1.0])
+    phase = 2 * math.pi * (X + Y)
+    # spatial derivative of the primitives along x and y (the wave depends on x + y only)
+    dbperp_dphase = amp * (-np.sin(phase)[None] * e1[:, None, None] + np.cos(phase)[None] * e2[:, None, None])
+    dWdx = np.zeros_like(W)
+    dWdx[1:4, :, :, 0] = -dbperp_dphase * 2 * math.pi / math.sqrt(rho)
+    dWdx[4:7, :, :, 0] = dbperp_dphase * 2 * math.pi
+    Wb = W.copy()
+    Wb[1:4] += np.asarray(u0)[:, None, None, None]
+    dWb = dW - (u0[0] + u0[1]) * dWdx
+    return Wb, dWb
+
+
+def test_boosted_alfven_wave_energy_converges():
+    """Every component of the residual of the Galilean-boosted Alfven wave,
+    the energy included, converges to the exact dU/dt at second order.  The
+    boost u0 has parts along and across k, so (V.B) varies along the wave and
+    the magnetic work term -B_n (V.B) of the energy flux (Sect. 2.2) enters
+    dE/dt; the kinetic-energy flux of the boost enters the momentum too."""
+    u0 = np.array([0.35, -0.15, 0.25])
+    errs = []
+    for n in (8, 16, 32, 64):
+        g = oracle.box(n, n, 1, limiter="vanalbada", gamma=5.0 / 3.0)
+        W, dW = _boosted_alfven_state(g, u0)
+        U = ci.prim_to_cons(W, g.gamma)
+        R = oracle.residual(g, U)["R"]
+        exact = _dcons_dt(W, dW, g.gamma)
+        assert np.abs(exact[7]).max() > 0.05
+        errs.append([np.mean(np.abs(R[v] - exact[v])) for v in range(8)])
+    errs = np.array(errs)
+    # rho is uniform and stays so: its residual is round-off at every size
+    assert errs[:, 0].max() < 1e-12
+    for v in range(1, 8):
+        if v == 3 and errs[-1, v] < 1e-12:
+            continue
+        order = math.log2(errs[-2, v] / errs[-1, v])
+        assert order > 1.85, (v, errs[:, v])
+    # the energy error is small against the energy change itself
+    assert errs[-1, 7] < 1e-2 * np.mean(np.abs(exact[7]))
 
 
 def _riemann_state(g):
