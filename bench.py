@@ -18,6 +18,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -35,6 +36,7 @@ WORKLOAD = "coronal shell 128x64x128 (r in [1,21.5] geometric, full sphere), Par
 SHAPE = (128, 64, 128)
 BYTES_PER_CELL = {"fp32": 72, "fp64": 144}     # read 9 + write 9 values per cell
 N_ROTATE = 4                                    # input/output sets rotated between steps
+MIN_TIMED_S = 0.3                               # shortest headline timed region (clock sampling)
 KERNEL_SOURCES = ["paper_2209_04481_gb300/csrc/residual.cuh",
                   "paper_2209_04481_gb300/csrc/mhd_device.cuh",
                   "paper_2209_04481_gb300/csrc/residual_launch.cuh",
@@ -340,20 +342,32 @@ def run_gb300(args):
     g32, Us, Rs, norms, dtmin, calls = make(args.only_headline or "fp32")
     steps, warmup = args.steps, max(3, args.warmup)
     graph, e0, e1 = time_graph(torch, stream, calls, steps, warmup)
+    # The clock sampler polls nvidia-smi every 50 ms, so the timed region
+    # replays the graph of `steps` launches as often as needed to last at
+    # least MIN_TIMED_S; every replay is timed (timed_steps = replays x steps).
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        graph.replay()
+        e1.record(stream)
+    torch.cuda.synchronize(device)
+    replays = max(1, int(math.ceil(MIN_TIMED_S / max(e0.elapsed_time(e1) / 1e3, 1e-9))))
+    replays = int(max_over_ranks(dist, float(replays), device))
     barrier(dist, device)
     torch.cuda.synchronize(device)
     with ClockSampler(local) as clocks:
         with torch.cuda.stream(stream):
             e0.record(stream)
-            graph.replay()
+            for _ in range(replays):
+                graph.replay()
             e1.record(stream)
         torch.cuda.synchronize(device)
     barrier(dist, device)
+    timed_steps = replays * steps
     sec = e0.elapsed_time(e1) / 1e3
     sec_max = max_over_ranks(dist, sec, device)
     g32.sync_status(stream)
-    value = aggregate([ncell * steps] * world, [sec_max])
-    kern_sec = sec / steps                     # one kernel launch per step
+    value = aggregate([ncell * timed_steps] * world, [sec_max])
+    kern_sec = sec / timed_steps               # one kernel launch per step
     peak, peak_kind = measured_peaks()
     achieved = BYTES_PER_CELL["fp32"] * ncell / kern_sec / 1e9
     traffic = profiled_traffic()
@@ -367,7 +381,8 @@ def run_gb300(args):
         pts = measure_pseudo_time(torch, g32, U0, device, stream, steps)
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
-                              "steps": steps, "warmup": warmup, "ms_per_step": sec_max * 1e3 / steps,
+                              "steps": steps, "warmup": warmup, "ms_per_step": sec_max * 1e3 / timed_steps,
+                              "timed_steps": timed_steps, "graph_replays": replays,
                               "higher_is_better": True, "pseudo_time_step": pts,
                               "note": "headline and pseudo-time step only (profiling run)"}), flush=True)
         g32.close()
@@ -379,7 +394,9 @@ def run_gb300(args):
             roofline = {"bound": "alu", "note": "FP64 residual: FP64-pipe bound"}
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
-                              "steps": steps, "warmup": warmup, "ms_per_step": sec_max * 1e3 / steps,
+                              "steps": steps, "warmup": warmup, "ms_per_step": sec_max * 1e3 / timed_steps,
+                              "timed_steps": timed_steps, "graph_replays": replays,
+                              "clocks": clocks.summary(),
                               "higher_is_better": True, "roofline": roofline,
                               "note": "headline only (profiling run)"}), flush=True)
         if dist is not None:
@@ -439,20 +456,23 @@ def run_gb300(args):
 
     result = {
         "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
-        "steps": steps, "warmup": warmup, "ms_per_step": sec_max * 1e3 / steps,
+        "steps": steps, "warmup": warmup, "ms_per_step": sec_max * 1e3 / timed_steps,
+        "timed_steps": timed_steps, "graph_replays": replays,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "cells": ncell, "precision": "fp32-bulk (FP64 "
                    "pressure recovery in low-beta cells, FP64 norms)", "limiter": "vanalbada",
                    "l2": f"{N_ROTATE} rotating input/output sets "
                          f"({N_ROTATE * 72 * ncell / 1e6:.0f} MB > L2)",
-                   "timing": "one CUDA graph of all timed steps, CUDA events on the launch stream",
+                   "timing": f"a CUDA graph of the {steps} steps, replayed {replays} times in the timed "
+                             f"region ({timed_steps} launches, >= {MIN_TIMED_S} s for the clock sampler), "
+                             "CUDA events on the launch stream",
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline,
         "alu_roofline": alu_roofline(),
         "hbm_gbs": achieved,
         "e2e": e2e,
-        "gpu_launches": steps,
+        "gpu_launches": timed_steps,
         "clocks": clocks.summary(),
         "fp64": fp64,
         "pseudo_time_step": pts,
@@ -651,12 +671,17 @@ def cpu_baseline(U0, Br, info, R32=None, R64=None, budget_s=15.0):
           "sample": f"{len(times)} full 128x64x128 residual evaluations (FP64 C++, one thread)"}
     err = {}
     scale = ref["scale"].reshape(9, -1).max(axis=1)
+    # per-cell scale: the cell's flux magnitude plus the rate at which its
+    # state changes at the CFL limit, |U_c| / dt_c
+    cscale = (ref["scale"] + np.abs(U0) / oracle.local_dt(og, U0)[None]).reshape(9, -1)
     names = ["rho", "mx", "my", "mz", "Bx", "By", "Bz", "E", "psi"]
     for tag, R in (("fp32", R32), ("fp64", R64)):
         if R is not None:
-            e = np.abs(R.reshape(9, -1) - ref["R"].reshape(9, -1)).max(axis=1) / scale
-            err[tag] = {n: float(x) for n, x in zip(names, e)}
+            d = np.abs(R.reshape(9, -1) - ref["R"].reshape(9, -1))
+            err[tag] = {n: float(x) for n, x in zip(names, d.max(axis=1) / scale)}
+            err[tag + "_per_cell"] = {n: float(x) for n, x in zip(names, (d / cscale).max(axis=1))}
     err["metric"] = "max_cells |R - R_oracle| / max_cells (1/V) sum_f |F*_v||S_f| per variable"
+    err["metric_per_cell"] = "max_cells |R - R_oracle|_c / ((1/V_c) sum_f |F*_v||S_f| + |U_c| / dt_c) per variable"
     return cb, err
 
 

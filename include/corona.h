@@ -56,7 +56,20 @@ typedef enum {
 
 typedef enum { CRN_FP64 = 0, CRN_FP32_BULK = 1 } crn_precision;
 typedef enum { CRN_LIM_NONE = 0, CRN_LIM_MINMOD = 1, CRN_LIM_VANALBADA = 2 } crn_limiter;
-typedef enum { CRN_KERNEL_TILED = 0, CRN_KERNEL_CELLWISE = 1 } crn_kernel;
+/* Residual kernel.  TILED (default) and TILED_REGS: the tiled kernel, raw
+ * state prefetched in registers by plain per-thread loads (any shape, FP32 and
+ * FP64).  STAGED (FP32_BULK only): each plane's own 8 x 32 block arrives by a
+ * TMA tensor copy and the halo by cp.async; it needs n_theta a multiple of 8,
+ * n_phi a multiple of 32 and a 16-byte aligned state, else the tiled kernel
+ * runs.  It computes the same residual and is slower on GB300 (127 us against
+ * 86 us on 128 x 64 x 128).  CELLWISE: a simple reference kernel, one thread
+ * per cell.  crn_last_kernel reports the kernel that ran. */
+typedef enum {
+  CRN_KERNEL_TILED = 0,
+  CRN_KERNEL_CELLWISE = 1,
+  CRN_KERNEL_TILED_REGS = 2,
+  CRN_KERNEL_STAGED = 3
+} crn_kernel;
 /* Inner-boundary formulation (Sect. 3.2): LOW_E: B_r prescribed, B_theta and
  * B_phi Neumann, V_b parallel to B_b (E_b = 0), |V_b| from the interior
  * velocity projected on B_b.  LARGE_E: the Wind-Predict form, B_r and B_theta
@@ -78,7 +91,7 @@ typedef struct {
   int32_t n_r, n_theta, n_phi;  /* cells; n_phi even and a multiple of 8         */
   int32_t precision;            /* crn_precision                                 */
   int32_t limiter;              /* crn_limiter                                   */
-  int32_t kernel;               /* crn_kernel (CELLWISE: simple reference kernel) */
+  int32_t kernel;               /* crn_kernel                                    */
   double r_in, r_out;           /* shell radii, 0 < r_in < r_out                 */
   double gamma;                 /* ratio of specific heats, > 1                  */
   double c_h;                   /* GLM cleaning speed, >= 0                      */
@@ -196,12 +209,18 @@ int crn_pseudo_time_step(crn_grid* g, double* U64_dev, int32_t nsteps, double cf
  * device, with that device current, resolves the array's address
  * (cudaGetSymbolAddress) and sets kernel attributes: make it before any
  * stream capture.  A call whose geometry fields (sizes, precision, radii, g0)
- * differ from the previous call's rebuilds the geometry on the stream first.
- * Every call clears the counter and error word it uses and shares the array:
- * calls that overlap on the GPU race and must be serialised by the caller.
- * Kernel-detected non-physical states are not reported (no error word is
- * returned); they show up as non-finite norms.  Calls no cudaMalloc,
- * cudaFree or other allocating routine.  Asynchronous on `stream`. */
+ * differ from the previous call's rebuilds the geometry on the stream first;
+ * a call made while `stream` is being captured records the geometry build
+ * with its residual, and from then on every call on that device rebuilds the
+ * geometry (a replay may have rebuilt another).  Every call clears the
+ * counter and error word it uses
+ * and shares the array: calls that overlap on the GPU race and must be
+ * serialised by the caller.  Non-physical states (rho <= 0, p <= 0) are not
+ * reported by this entry point: there is no status call for it, and such a
+ * state need not make the residual or the norms non-finite, so a caller that
+ * needs the check makes it on the state.  Van Albada needs lim_eps > 0
+ * (CRN_E_ARG otherwise).  Calls no cudaMalloc, cudaFree or other allocating
+ * routine.  Asynchronous on `stream`. */
 int crn_residual_static(const crn_grid_desc* d, const double* Br_dev, const void* U_dev,
                         void* R_dev, double* norms9_dev, double* dtmin_dev, void* stream);
 
@@ -379,7 +398,9 @@ int crn_adjoint_solve(crn_grid* g, const double* U64_dev, const double* gbar_dev
 /* Synchronise the stream, then read and clear the grid's device error word.
  * Returns CRN_E_NONPHYSICAL if a kernel saw a non-physical state since the
  * last call (crn_last_bad_cell gives the lowest flagged cell index,
- * k * n_theta * n_phi + j * n_phi + i), CRN_E_CUDA on a CUDA error. */
+ * k * n_theta * n_phi + j * n_phi + i), CRN_E_TIMEOUT if a kernel's bounded
+ * wait for an asynchronous (TMA) copy gave up (its outputs are then invalid),
+ * CRN_E_CUDA on a CUDA error. */
 int crn_sync_status(crn_grid* g, void* stream);
 
 /* Lowest flat cell index flagged by the last crn_sync_status, -1 if none. */
@@ -390,6 +411,11 @@ const char* crn_last_error(void);
 
 /* Number of kernel launches the last compute call of this grid issued. */
 int32_t crn_last_launch_count(const crn_grid* g);
+
+/* The residual kernel (crn_kernel: CELLWISE, TILED_REGS or STAGED) that the
+ * last residual evaluation of this grid launched; -1 before the first one or
+ * for a NULL grid. */
+int32_t crn_last_kernel(const crn_grid* g);
 
 #ifdef __cplusplus
 }

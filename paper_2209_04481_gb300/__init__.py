@@ -19,10 +19,11 @@ import os
 import threading
 
 __all__ = ["Grid", "Residual", "residual", "load_library", "CoronaError", "FP64", "FP32_BULK",
-           "LIMITERS", "KERNEL_TILED", "KERNEL_CELLWISE", "exported_symbols"]
+           "LIMITERS", "KERNEL_TILED", "KERNEL_CELLWISE", "KERNEL_TILED_REGS", "KERNEL_STAGED",
+           "exported_symbols"]
 
 FP64, FP32_BULK = 0, 1
-KERNEL_TILED, KERNEL_CELLWISE = 0, 1
+KERNEL_TILED, KERNEL_CELLWISE, KERNEL_TILED_REGS, KERNEL_STAGED = 0, 1, 2, 3
 LIMITERS = {"none": 0, "minmod": 1, "vanalbada": 2}
 _STATUS = {0: "CRN_OK", 1: "CRN_E_ARG", 2: "CRN_E_CUDA", 3: "CRN_E_NONPHYSICAL",
            4: "CRN_E_TIMEOUT", 5: "CRN_E_STATE"}
@@ -115,6 +116,7 @@ def load_library(build_if_needed: bool = True):
             "crn_last_bad_cell": (ctypes.c_int64, [vp]),
             "crn_last_error": (ctypes.c_char_p, []),
             "crn_last_launch_count": (i32, [vp]),
+            "crn_last_kernel": (i32, [vp]),
             "crn_boundary_efield": (ctypes.c_int, [vp, vp, vp, vp]),
             "crn_efield": (ctypes.c_int, [vp, vp, vp, vp]),
             "crn_nk_options_default": (ctypes.c_int, [ctypes.POINTER(NkOptions)]),
@@ -185,7 +187,8 @@ class Grid:
         _check(lib.crn_grid_desc_default(ctypes.byref(d), n_r, n_theta, n_phi))
         d.precision = {"fp64": FP64, "fp32": FP32_BULK, "fp32_bulk": FP32_BULK}[precision]
         d.limiter = LIMITERS[limiter]
-        d.kernel = {"tiled": KERNEL_TILED, "cellwise": KERNEL_CELLWISE}[kernel]
+        d.kernel = {"tiled": KERNEL_TILED, "cellwise": KERNEL_CELLWISE, "tiled_regs": KERNEL_TILED_REGS,
+                    "staged": KERNEL_STAGED}[kernel]
         if "inner_bc" in kw and isinstance(kw["inner_bc"], str):
             kw["inner_bc"] = {"low_e": 0, "large_e": 1, "low_e_wp": 2}[kw["inner_bc"]]
         for k, v in kw.items():
@@ -221,6 +224,12 @@ class Grid:
     @property
     def last_launch_count(self):
         return int(_lib.crn_last_launch_count(self._h))
+
+    @property
+    def last_kernel(self):
+        """Kernel of the last residual evaluation: "cellwise", "tiled_regs" or "staged"."""
+        k = int(_lib.crn_last_kernel(self._h))
+        return {KERNEL_CELLWISE: "cellwise", KERNEL_TILED_REGS: "tiled_regs", KERNEL_STAGED: "staged"}.get(k)
 
     # -- calls ---------------------------------------------------------------
     @property

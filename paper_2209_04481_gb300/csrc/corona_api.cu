@@ -50,7 +50,8 @@ int validate(const crn_grid_desc* d) {
     return fail(CRN_E_ARG, "precision must be CRN_FP64 or CRN_FP32_BULK");
   if (d->limiter < CRN_LIM_NONE || d->limiter > CRN_LIM_VANALBADA)
     return fail(CRN_E_ARG, "unknown limiter");
-  if (d->kernel != CRN_KERNEL_TILED && d->kernel != CRN_KERNEL_CELLWISE)
+  if (d->kernel != CRN_KERNEL_TILED && d->kernel != CRN_KERNEL_CELLWISE && d->kernel != CRN_KERNEL_TILED_REGS &&
+      d->kernel != CRN_KERNEL_STAGED)
     return fail(CRN_E_ARG, "unknown kernel variant");
   if (!(finite(d->r_in) && finite(d->r_out) && d->r_in > 0.0 && d->r_out > d->r_in))
     return fail(CRN_E_ARG, "need 0 < r_in < r_out");
@@ -354,7 +355,23 @@ int crn_grid_create(const crn_grid_desc* d, crn_grid** out) {
     g->cfg.kchunk_tiled = kc;
     g->cfg.num_sms = std::max(nsm, 1);
     g->cfg.update_per_sm = crn::update_blocks_per_sm(d->precision != CRN_FP64);
-    const int64_t tiled_blocks = ntiles * ((d->n_r + kc - 1) / kc);
+    int64_t tiled_blocks = ntiles * ((d->n_r + kc - 1) / kc);
+    // the TMA-staged FP32 kernel, on request: whole 8 x 32 blocks only
+    if (d->precision == CRN_FP32_BULK && d->kernel == CRN_KERNEL_STAGED &&
+        crn::staged_shape_ok(d->n_theta, d->n_phi)) {
+      const int sper = crn::staged_ctas_per_sm_fp32(d->limiter);
+      if (sper > 0) {
+        const int64_t st = crn::staged_tiles(d->n_theta, d->n_phi);
+        int kcs = crn::choose_kchunk_balanced(d->n_r, st, (long long)std::max(nsm, 1) * sper);
+        if (const char* env = std::getenv("CRN_KCHUNK")) {
+          const int v = std::atoi(env);
+          if (v >= 1) kcs = v;
+        }
+        g->cfg.staged = true;
+        g->cfg.kchunk_staged = kcs;
+        tiled_blocks = std::max<int64_t>(tiled_blocks, st * ((d->n_r + kcs - 1) / kcs));
+      }
+    }
     const int64_t cell_blocks = (g->shape.ncell + 255) / 256;
     g->max_blocks = (size_t)std::max<int64_t>(std::max<int64_t>(tiled_blocks, cell_blocks), 4 * 152 * 8);
   }
@@ -525,7 +542,8 @@ int crn_sync_status(crn_grid* g, void* stream) {
   if (e == cudaSuccess) e = cudaMemset(g->err_cell, 0xff, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_fail(e, "crn_sync_status");
-  g->last_bad_cell = flags ? (int64_t)cell : -1;
+  g->last_bad_cell = (flags & 1u) ? (int64_t)cell : -1;
+  if (flags & 2u) return fail(CRN_E_TIMEOUT, "a kernel's bounded wait for an asynchronous copy gave up");
   if (flags) {
     char buf[160];
     std::snprintf(buf, sizeof(buf), "non-physical or non-finite state at cell %lld",
@@ -541,5 +559,7 @@ int64_t crn_last_bad_cell(const crn_grid* g) { return g ? g->last_bad_cell : -1;
 const char* crn_last_error(void) { return g_last_error.c_str(); }
 
 int32_t crn_last_launch_count(const crn_grid* g) { return g ? g->last_launches : 0; }
+
+int32_t crn_last_kernel(const crn_grid* g) { return g ? g->last_kernel : -1; }
 
 }  // extern "C"

@@ -31,6 +31,8 @@ struct LaunchCfg {
   int kchunk_tiled = 16;  // radial planes per CTA of the tiled kernel
   int num_sms = 152;      // streaming multiprocessors of the grid's device
   int update_per_sm = 2;  // resident blocks per SM of the pseudo-time update
+  bool staged = false;    // FP32 residuals use the TMA-staged kernel (on request)
+  int kchunk_staged = 16; // radial planes per CTA of the staged kernel
 };
 
 }  // namespace crn
@@ -58,6 +60,7 @@ struct crn_grid {
   crn::HostPipe* pipe = nullptr;   // host-buffer staging (allocated by the first host batch)
   int64_t last_bad_cell = -1;
   int32_t last_launches = 0;
+  int32_t last_kernel = -1;        // crn_kernel of the last residual launch
   crn::LaunchCfg cfg;
 };
 
@@ -111,6 +114,11 @@ int report_error(int code, const char* msg);
 // (after prepare_*), 0 on error
 int tiled_ctas_per_sm_fp64(int limiter);
 int tiled_ctas_per_sm_fp32(int limiter);
+// the TMA-staged FP32 kernel: whether a shape tiles into its blocks, its
+// block count, and its resident CTAs per SM
+bool staged_shape_ok(int nt, int np);
+int staged_tiles(int nt, int np);
+int staged_ctas_per_sm_fp32(int limiter);
 
 // Radial planes per CTA of the tiled kernel: the largest chunk count whose
 // CTAs all fit in one wave of `slots` resident CTAs (fewer planes per CTA

@@ -4,6 +4,7 @@
 namespace crn {
 cudaError_t launch_residual_fp64(crn_grid* g, const double* U, double* R, double* norms_user,
                                  double* dt_user, cudaStream_t st, int* nlaunch) {
+  g->last_kernel = g->d.kernel == CRN_KERNEL_CELLWISE ? CRN_KERNEL_CELLWISE : CRN_KERNEL_TILED_REGS;
   return launch_residual_t<double>(g, U, R, norms_user, dt_user, st, nlaunch);
 }
 size_t tiled_smem_fp64() { return tiled_smem_t<double>(); }

@@ -15,7 +15,9 @@
 // their shared memory; make that first call before any stream capture.  When
 // the descriptor differs from the one the geometry was last built for, the
 // geometry is rebuilt on the device, on the caller's stream, before the
-// residual kernel.  All calls share the array and it keeps the last call's
+// residual kernel.  A call recorded in a CUDA graph records the geometry build
+// with it; after that, every call on the device rebuilds the geometry, since a
+// replay may have overwritten it.  All calls share the array and it keeps the last call's
 // contents: calls whose kernels overlap on the GPU (two streams, two host
 // threads) race on it and must be serialised by the caller.
 #include <algorithm>
@@ -67,6 +69,7 @@ struct DeviceSlot {
   unsigned char* base = nullptr;  // device address of g_scratch on this device
   bool geo_valid = false;
   crn_grid_desc geo_desc{};
+  bool captured = false;  // a call on this device was recorded in a graph
 };
 
 std::mutex g_mu;
@@ -93,6 +96,8 @@ int validate_static(const crn_grid_desc* d) {
   if (!(std::isfinite(d->c_h) && d->c_h >= 0.0)) return fail(CRN_E_ARG, "c_h must be >= 0");
   if (!std::isfinite(d->g0)) return fail(CRN_E_ARG, "g0 must be finite");
   if (!(std::isfinite(d->lim_eps) && d->lim_eps >= 0.0)) return fail(CRN_E_ARG, "lim_eps must be >= 0");
+  if (d->limiter == CRN_LIM_VANALBADA && !(d->lim_eps > 0.0))
+    return fail(CRN_E_ARG, "the van Albada limiter needs lim_eps > 0 (its smooth form is 0/0 where both slopes vanish)");
   if (!std::isfinite(d->outer_rho_exp) || !std::isfinite(d->outer_br_exp))
     return fail(CRN_E_ARG, "outer exponents must be finite");
   if (!(d->rho_b > 0.0 && d->p_b > 0.0 && std::isfinite(d->rho_b) && std::isfinite(d->p_b)))
@@ -339,7 +344,16 @@ extern "C" int crn_residual_static(const crn_grid_desc* d, const double* Br_dev,
     slot.base = static_cast<unsigned char*>(p);
     slot.ready = true;
   }
-  if (!slot.geo_valid || !same_geometry(slot.geo_desc, *d)) {
+  // A call recorded into a graph records its own geometry build, so that a
+  // replay does not depend on calls made after the capture.  Since any replay
+  // may then rebuild the array with its own geometry, every uncaptured call
+  // on a device where a call was captured rebuilds the geometry too.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(st, &cap);
+  if (e != cudaSuccess) return fail(CRN_E_CUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(e));
+  const bool capturing = cap != cudaStreamCaptureStatusNone;
+  if (capturing) slot.captured = true;
+  if (slot.captured || !slot.geo_valid || !same_geometry(slot.geo_desc, *d)) {
     const int64_t work = (int64_t)(d->n_theta + 1) * d->n_phi;
     const unsigned nb = (unsigned)std::min<int64_t>((work + 255) / 256, 1024);
     if (d->precision == CRN_FP64)
@@ -351,7 +365,7 @@ extern "C" int crn_residual_static(const crn_grid_desc* d, const double* Br_dev,
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail(CRN_E_CUDA, std::string("geometry launch: ") + cudaGetErrorString(e));
     slot.geo_desc = *d;
-    slot.geo_valid = true;
+    slot.geo_valid = !slot.captured;
   }
   if (d->precision == CRN_FP64)
     return run<double>(*d, slot.base, Br_dev, U_dev, R_dev, norms9_dev, dtmin_dev, st);

@@ -32,3 +32,58 @@ def rel_err(R, R_ref, scale):
     R_ref = np.asarray(R_ref).reshape(9, -1)
     scale = np.asarray(scale).reshape(9, -1)
     return np.abs(R - R_ref).max(axis=1) / scale.max(axis=1)
+
+
+# ---------------------------------------------------------------------------
+# FP32-bulk error bounds, per variable group (rho, m, B, E, psi)
+# ---------------------------------------------------------------------------
+def per_var(rho, m, B, E, psi):
+    """Nine per-variable values from the five groups (rho, rho V, B, E, psi)."""
+    return np.array([rho, m, m, m, B, B, B, E, psi])
+
+
+# Global metric (rel_err, max |dR| over max M): measured maxima over the parity
+# workloads, 128 x 64 x 128 included, are rho 4.7e-7, m 2.8e-7, B 3.0e-7,
+# E 2.7e-7, psi 2.0e-7; the bounds keep a 6-10x margin.
+FP32_GLOBAL = per_var(rho=3e-6, m=2e-6, B=2e-6, E=2e-6, psi=2e-6)
+# Per-cell metric (cell_err): |dR_c| over the cell's own scale M_c + |U_c| / dt_c
+# (flux magnitude plus the rate at which the cell's state changes at the CFL
+# limit).  Measured maxima rho 3.5e-7, m 1.6e-6, B 1.1e-6, E 5.4e-7, psi 3.2e-7;
+# the bounds keep a 6-10x margin.  (Against M_c alone the per-cell error of B
+# and E reaches 1e-3 / 2e-4 in the slow low-beta base near the inner boundary,
+# where the combined flux of a variable nearly cancels while the reconstructed
+# states it is made of are O(1).)
+FP32_CELL = per_var(rho=3e-6, m=1e-5, B=1e-5, E=5e-6, psi=3e-6)
+# norms against the oracle's (measured <= 1.8e-7), the FP32 accumulation of
+# the GPU's own R against its FP64 sum (measured <= 2.8e-8; per-thread sums of
+# at most 16 terms and a 5-level warp tree in FP32 bound it by ~1.2e-6), and
+# the step bound (measured <= 2.2e-7)
+FP32_NORM_RTOL = 2e-6
+FP32_NORM_ACCUMULATION = 1e-6
+FP32_DTMIN_RTOL = 2e-6
+
+
+def cell_err(R, R_ref, scale, U, dt_cell):
+    """Per-variable max over cells of |R - R_ref| / (M_c + |U_c| / dt_c)."""
+    R = np.asarray(R, dtype=np.float64).reshape(9, -1)
+    R_ref = np.asarray(R_ref).reshape(9, -1)
+    s = (np.asarray(scale) + np.abs(np.asarray(U)) / np.asarray(dt_cell)[None]).reshape(9, -1)
+    return (np.abs(R - R_ref) / s).max(axis=1)
+
+
+def check_fp32(R, ref, og, U, norms=None, dtmin=None):
+    """Every FP32-bulk bound above for one residual evaluation: R against the
+    oracle's (global and per cell, per variable), the norms against the
+    oracle's and against the FP64 sum of the GPU's own R, and the step bound."""
+    R = np.asarray(R, dtype=np.float64)
+    g = rel_err(R, ref["R"], ref["scale"])
+    assert np.all(g <= FP32_GLOBAL), ("global", g)
+    c = cell_err(R, ref["R"], ref["scale"], U, oracle.local_dt(og, U))
+    assert np.all(c <= FP32_CELL), ("per cell", c)
+    if norms is not None:
+        norms = np.asarray(norms)
+        np.testing.assert_allclose(norms, ref["norms"], rtol=FP32_NORM_RTOL)
+        own = np.sqrt((R.reshape(9, -1) ** 2).sum(axis=1))
+        np.testing.assert_allclose(norms, own, rtol=FP32_NORM_ACCUMULATION)
+    if dtmin is not None:
+        assert abs(dtmin - ref["dtmin"]) <= FP32_DTMIN_RTOL * ref["dtmin"]

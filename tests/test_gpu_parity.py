@@ -3,22 +3,22 @@
 Error metric per variable: max_c |R_gpu - R_oracle| / max_c M_c with M the
 oracle's flux-magnitude scale (1/V) sum_f |F*_v| |S_f| -- R is a small
 difference of large face fluxes, so a per-cell relative error is meaningless.
-Bars: FP64 <= 1e-12; FP32-bulk <= the per-variable bound FP32_BOUND below.
+Bars: FP64 <= 1e-12; FP32-bulk: the per-variable global and per-cell bounds
+of tests/_util.py (check_fp32), plus norms, their FP32 accumulation and dtmin.
 """
 import numpy as np
 import pytest
 
 import coronal_inputs as ci
 import oracle
-from _util import oracle_grid, problem, rel_err
+from _util import check_fp32, oracle_grid, problem, rel_err
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 FP64_BOUND = 1e-12
-# FP32 bulk: single-precision storage of U (E rounded to 2^-24 relative) and
-# FP32 flux arithmetic; bound per variable (rho, m, B, E, psi), measured
-# maxima on the tested workloads are ~1e-6 and the bar keeps a 10x margin.
+# FP32-bulk tests elsewhere in the suite that go through several kernels (VJP,
+# Newton-Krylov) keep this looser bar on the global metric
 FP32_BOUND = 2e-5
 
 
@@ -67,10 +67,7 @@ def test_fp32_bulk_parity(shape, limiter):
     U, Br = problem(shape, perturb=7)
     ref = reference(shape, U, Br, limiter)
     _, R, norms, dtmin = run_gpu(shape, U, Br, "fp32", limiter)
-    err = rel_err(R, ref["R"], ref["scale"])
-    assert np.all(err <= FP32_BOUND), err
-    np.testing.assert_allclose(norms, ref["norms"], rtol=1e-3)
-    assert dtmin == pytest.approx(ref["dtmin"], rel=1e-4)
+    check_fp32(R, ref, oracle_grid(shape, limiter=limiter), U, norms, dtmin)
 
 
 @pytest.mark.parametrize("precision,bound", [("fp64", FP64_BOUND), ("fp32", FP32_BOUND)])
@@ -81,10 +78,13 @@ def test_full_size_parity_128x64x128(precision, bound):
     shape = (128, 64, 128)
     ref = reference(shape, U, Br)
     _, R, norms, dtmin = run_gpu(shape, U, Br, precision)
+    if precision == "fp32":
+        check_fp32(R, ref, oracle_grid(shape), U, norms, dtmin)
+        return
     err = rel_err(R, ref["R"], ref["scale"])
     assert np.all(err <= bound), err
-    np.testing.assert_allclose(norms, ref["norms"], rtol=1e-10 if precision == "fp64" else 1e-3)
-    assert dtmin == pytest.approx(ref["dtmin"], rel=1e-12 if precision == "fp64" else 1e-4)
+    np.testing.assert_allclose(norms, ref["norms"], rtol=1e-10)
+    assert dtmin == pytest.approx(ref["dtmin"], rel=1e-12)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])

@@ -121,3 +121,33 @@ def test_radial_chunk_minimises_the_makespan(lib, nr, ntiles, slots):
     if (nr, ntiles, slots) == (128, 32, 152):
         assert kc == 29
     assert f(0, 1, 1, 3) == -1
+
+
+def test_static_entry_point_rejects_van_albada_without_eps(lib):
+    """crn_residual_static validates its descriptor on the host before any
+    device work, like crn_grid_create: the smooth van Albada form is 0/0
+    where both slopes vanish, so lim_eps must be > 0."""
+    f = lib.crn_residual_static
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.POINTER(pg.GridDesc)] + [ctypes.c_void_p] * 6
+    d = pg.GridDesc()
+    lib.crn_grid_desc_default(ctypes.byref(d), 8, 8, 32)
+    d.lim_eps = 0.0
+    assert f(ctypes.byref(d), None, None, None, None, None, None) == 1  # CRN_E_ARG
+    assert "lim_eps" in lib.crn_last_error().decode()
+    d.limiter = pg.LIMITERS["minmod"]     # other limiters ignore lim_eps
+    assert f(ctypes.byref(d), None, None, None, None, None, None) == 1
+    assert "NULL" in lib.crn_last_error().decode()
+
+
+def test_kernel_selector_values(lib):
+    """The descriptor accepts the tiled, cellwise, register-staged and
+    TMA-staged kernel values and rejects others before any device work."""
+    d = pg.GridDesc()
+    lib.crn_grid_desc_default(ctypes.byref(d), 8, 8, 32)
+    d.kernel = 7
+    h = ctypes.c_void_p()
+    assert lib.crn_grid_create(ctypes.byref(d), ctypes.byref(h)) == 1
+    assert "kernel" in lib.crn_last_error().decode()
+    assert (pg.KERNEL_TILED, pg.KERNEL_CELLWISE, pg.KERNEL_TILED_REGS, pg.KERNEL_STAGED) == (0, 1, 2, 3)
+    assert lib.crn_last_kernel(None) == -1
