@@ -254,35 +254,43 @@ def time_graph(torch, stream, fn_list, steps, warmup):
 # ---------------------------------------------------------------------------
 # the GB300 arm
 # ---------------------------------------------------------------------------
-def measure_pseudo_time(torch, g32, U0, device, stream, steps):
-    """Explicit pseudo-time update (FP32 bulk residual + FP64 master update),
-    in batches of 10 steps from the initial state (forward Euler at CFL 0.4
-    is only run for short stretches, as in the 10-step shell32 case)."""
+def measure_pseudo_time(torch, pg, U0, Br, p_b, device, stream, nsteps=200, seed=2209):
+    """Explicit pseudo-time stepping (FP32-bulk residual on the shadow + FP64
+    master update and res(a) monitor), nsteps consecutive steps at CFL 0.4
+    from the initial state, on the benchmark shell with the time-marching
+    inner boundary (low-E ghost with the prescribed Wind-Predict outflow
+    magnitude, Sect. 3.2), starting from the wind with the potential field of
+    the magnetogram."""
+    import coronal_inputs as ci
     ncell = U0[0].size
-    U0d = torch.from_numpy(U0.copy()).to(device)
-    U64 = U0d.clone()
-    batch, nbatch = 10, max(1, min(steps // 40, 20))
+    shape = U0.shape[1:]
+    # the time-marching start: the wind with the potential field of the magnetogram
+    Up, _ = ci.potential_background(*shape, seed=seed)
+    g = pg.Grid(*shape, precision="fp32", p_b=p_b, inner_bc="low_e_wp")
+    g.set_inner_boundary(torch.from_numpy(Br).to(device))
+    U64 = torch.from_numpy(Up).to(device)
+    res = torch.zeros((nsteps, 9), dtype=torch.float64, device=device)
     with torch.cuda.stream(stream):
-        g32.pseudo_time_step(U64, 3, 0.4, stream=stream)
-    stream.synchronize()
-    pts_sec = 0.0
-    for _ in range(nbatch):
-        with torch.cuda.stream(stream):
-            U64.copy_(U0d)
-            p0 = torch.cuda.Event(enable_timing=True)
-            p1 = torch.cuda.Event(enable_timing=True)
-            p0.record(stream)
-            g32.pseudo_time_step(U64, batch, 0.4, stream=stream)
-            p1.record(stream)
-        torch.cuda.synchronize(device)
-        pts_sec += p0.elapsed_time(p1) / 1e3
-    g32.sync_status(stream)
-    pts_steps = batch * nbatch
-    pts = {"value": ncell * pts_steps / pts_sec, "unit": "cell-updates/s",
-           "ms_per_step": pts_sec * 1e3 / pts_steps, "steps": pts_steps, "cfl": 0.4,
-           "launches_per_step": 2,
-           "note": "residual on the FP32 shadow + FP64 master update and res(a) monitor; "
-                   f"{nbatch} batches of {batch} steps from the initial state"}
+        g.pseudo_time_step(U64.clone(), 3, 0.4, stream=stream)     # warm-up on a copy
+        stream.synchronize()
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        g.pseudo_time_step(U64, nsteps, 0.4, res_log10=res, stream=stream)
+        p1.record(stream)
+    torch.cuda.synchronize(device)
+    sec = p0.elapsed_time(p1) / 1e3
+    g.sync_status(stream)
+    r = res.cpu()
+    pts = {"value": ncell * nsteps / sec, "unit": "cell-updates/s",
+           "ms_per_step": sec * 1e3 / nsteps, "steps": nsteps, "cfl": 0.4,
+           "launches_per_step": 2, "inner_bc": "low_e_wp",
+           "res_log10_first": [round(float(x), 3) for x in r[0]],
+           "res_log10_last": [round(float(x), 3) for x in r[-1]],
+           "all_finite": bool(torch.isfinite(r).all()),
+           "note": f"{nsteps} consecutive steps from the initial state in one call: residual on the FP32 "
+                   "shadow + FP64 master update and res(a) monitor"}
+    g.close()
     return pts
 
 
@@ -378,7 +386,7 @@ def run_gb300(args):
     R32 = Rs[(steps - 1) % N_ROTATE].double().cpu().numpy()
     del graph
     if args.only_pseudo_time:
-        pts = measure_pseudo_time(torch, g32, U0, device, stream, steps)
+        pts = measure_pseudo_time(torch, pg, U0, Br, info["p_b"], device, stream, seed=2209 + rank)
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
                               "steps": steps, "warmup": warmup, "ms_per_step": sec_max * 1e3 / timed_steps,
@@ -427,7 +435,7 @@ def run_gb300(args):
            "api": "Grid.residual_host_batch -> crn_residual_host_batch (pinned host buffers, "
                   "copies of consecutive steps overlapped with the residual)"}
 
-    pts = measure_pseudo_time(torch, g32, U0, device, stream, steps)
+    pts = measure_pseudo_time(torch, pg, U0, Br, info["p_b"], device, stream, seed=2209 + rank)
     g32.close()
     del Us, Rs
 
@@ -590,13 +598,15 @@ def run_nk(torch, pg, ci, device, stream, only=None, steps_cap=None):
 def run_ensemble(torch, pg, ci, device, stream, nsteps=200):
     """32 shells of uneven sizes (33.05 M cells) in one persistent launch:
     autotuned radial chunk, then nsteps ensemble residual evaluations timed
-    with CUDA events, and nsteps explicit pseudo-time steps (FP32-bulk
-    residual + FP64 master update) in batches of 10 from the initial states."""
+    with CUDA events, and nsteps consecutive explicit pseudo-time steps
+    (FP32-bulk residual + FP64 master update) from the initial states, all
+    members in one call.  Members use the time-marching inner boundary (low-E
+    ghost with the prescribed Wind-Predict outflow magnitude, Sect. 3.2)."""
     spec = ci.ensemble_members()
     gs, U32, U64s, U0s = [], [], [], []
     for shape, mseed in spec:
         U, Br, pb = ci.ensemble_member(shape, mseed)
-        g = pg.Grid(*shape, precision="fp32", p_b=pb)
+        g = pg.Grid(*shape, precision="fp32", p_b=pb, inner_bc="low_e_wp")
         g.set_inner_boundary(torch.from_numpy(Br).to(device))
         gs.append(g)
         U0s.append(torch.from_numpy(U).to(device))
@@ -604,45 +614,63 @@ def run_ensemble(torch, pg, ci, device, stream, nsteps=200):
     R32 = [torch.empty_like(u) for u in U32]
     cells = sum(g.ncell for g in gs)
     ens = pg.Ensemble(gs)
+
+    def timed_residual():
+        # the timed steps replay one captured CUDA graph of nsteps ensemble
+        # calls (each a counter memset and one persistent kernel per tile shape)
+        graph, e0, e1 = time_graph(torch, stream, [lambda: ens.residual(U32, R32, stream=stream)], nsteps, 3)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            graph.replay()
+            e1.record(stream)
+        torch.cuda.synchronize(device)
+        sec = e0.elapsed_time(e1) / 1e3
+        del graph
+        return {"value": cells * nsteps / sec, "unit": "cell-updates/s", "steps": nsteps,
+                "ms_per_step": 1e3 * sec / nsteps, "launches_per_step": ens.last_launch_count,
+                "timing": "one CUDA graph of all timed steps, CUDA events"}
+
+    before = timed_residual()                 # every member: 8 x 32 tiles, its own radial chunk
     with torch.cuda.stream(stream):
-        ens.residual(U32, R32, stream=stream)
         stream.synchronize()
         t0 = time.perf_counter()
         kchunk = ens.autotune(U32, R32, stream=stream)
         tune_s = time.perf_counter() - t0
-    # the timed steps replay one captured CUDA graph of nsteps ensemble calls
-    # (each a counter memset and the persistent kernel)
-    graph, e0, e1 = time_graph(torch, stream, [lambda: ens.residual(U32, R32, stream=stream)], nsteps, 3)
-    with torch.cuda.stream(stream):
-        e0.record(stream)
-        graph.replay()
-        e1.record(stream)
-    torch.cuda.synchronize(device)
-    sec = e0.elapsed_time(e1) / 1e3
-    del graph
+    classes = {}
+    for m, g in enumerate(gs):
+        tile, kc = ens.member_config(m)
+        key = f"{g.shape[1]}x{g.shape[2]}"
+        c = classes.setdefault(key, {"members": 0, "tile": list(tile), "kchunk": []})
+        c["members"] += 1
+        c["kchunk"].append(kc)
+    for c in classes.values():
+        c["kchunk"] = sorted(set(c["kchunk"]))
     res = {"members": len(gs), "cells": cells, "kchunk": kchunk, "autotune_s": tune_s,
-           "residual": {"value": cells * nsteps / sec, "unit": "cell-updates/s", "steps": nsteps,
-                        "ms_per_step": 1e3 * sec / nsteps, "launches_per_step": 1,
-                        "timing": "one CUDA graph of all timed steps, CUDA events"}}
+           "autotuned": classes, "residual_before_autotune": before, "residual": timed_residual()}
     U64s = [u.clone() for u in U0s]
-    batch, nb = 10, nsteps // 10
-    pts = 0.0
-    for _ in range(nb):
-        with torch.cuda.stream(stream):
-            for u, u0 in zip(U64s, U0s):
-                u.copy_(u0)
-            p0 = torch.cuda.Event(enable_timing=True)
-            p1 = torch.cuda.Event(enable_timing=True)
-            p0.record(stream)
-            ens.pseudo_time_step(U64s, batch, 0.4, stream=stream)
-            p1.record(stream)
-        torch.cuda.synchronize(device)
-        pts += p0.elapsed_time(p1) / 1e3
-    res["pseudo_time_step"] = {"value": cells * batch * nb / pts, "unit": "cell-updates/s",
-                               "steps": batch * nb, "ms_per_step": 1e3 * pts / (batch * nb),
-                               "launches_per_step": 2}
+    logs = torch.zeros((len(gs), 9), dtype=torch.float64, device=device)
+    with torch.cuda.stream(stream):
+        ens.pseudo_time_step([u.clone() for u in U0s], 3, 0.4, stream=stream)   # warm-up on copies
+        stream.synchronize()
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        ens.pseudo_time_step(U64s, nsteps, 0.4, res_log10=logs, stream=stream)
+        p1.record(stream)
+    torch.cuda.synchronize(device)
+    pts = p0.elapsed_time(p1) / 1e3
+    for g in gs:
+        g.sync_status(stream)
+    lg = logs.cpu()
+    res["pseudo_time_step"] = {"value": cells * nsteps / pts, "unit": "cell-updates/s",
+                               "steps": nsteps, "ms_per_step": 1e3 * pts / nsteps,
+                               "launches_per_step": 2, "consecutive": True,
+                               "all_members_finite": bool(torch.isfinite(lg).all()),
+                               "res_log10_last_max": round(float(lg.max()), 3),
+                               "res_log10_last_min": round(float(lg.min()), 3)}
     res["workload"] = ("32 shells, N_r ~ U{48..192}, (N_theta, N_phi) in {24x48, 48x96, 96x192} "
-                       "(default_rng(5)); Parker + dipole, magnetogram seed = member index")
+                       "(default_rng(5)); Parker + dipole, magnetogram seed = member index; "
+                       "potential-field start, low-E inner boundary with the prescribed outflow magnitude")
     ens.close()
     for g in gs:
         g.close()

@@ -208,6 +208,74 @@ def potential_field(n_theta, n_phi, lmax=15, seed=2209, target_max=5.0, dipole_o
     return np.stack([br, bt])
 
 
+def potential_background(n_r, n_theta, n_phi, lmax=15, seed=2209, target_max=5.0, dipole_only=False,
+                         efree=False, gamma=GAMMA, g0=G0_SOLAR, r_c=PARKER_RC, r_in=R_IN, r_out=R_OUT,
+                         dtheta=1e-6):
+    """Parker wind with the source-free potential field of the magnetogram.
+
+    The field is B = -grad Phi, Phi = cos(theta) / (2 r^2) + s sum_lm a_lm
+    r^-(l+1) Y_lm / (l + 1) with the coefficients and scale of
+    ``magnetogram(...)``, so that B_r at r = r_in = 1 is that magnetogram: the
+    dipole part is the aligned dipole of ``background`` and each further
+    multipole falls as r^-(l+2).  It stands in for the PFSS initial field the
+    paper starts from (Sect. 3.1): the initial state then agrees with the
+    prescribed inner B_r instead of jumping from it to the dipole.
+    ``efree`` turns the wind velocity along B as in ``background``.
+    Returns (U, info) like ``background``."""
+    U, info = background(n_r, n_theta, n_phi, gamma=gamma, g0=g0, r_c=r_c, r_in=r_in, r_out=r_out)
+    W = info["W"].copy()
+    if not dipole_only:
+        rc, tc, pc = cell_centres(n_r, n_theta, n_phi, r_in, r_out)
+        T, P = np.meshgrid(tc, pc, indexing="ij")
+        scale = _magnetogram_scale(n_theta, n_phi, lmax, seed, target_max)
+        rng = np.random.default_rng(seed)
+        ys = real_sh(lmax, T, P)
+        hi = real_sh(lmax, T + dtheta, P)
+        lo = real_sh(lmax, T - dtheta, P)
+        by_l = {}
+        for (l, m, Y), (_, _, Yp), (_, _, Ym) in zip(ys, hi, lo):
+            if l == 0:
+                continue
+            a = scale * rng.standard_normal() / l
+            gr, gt, gp = by_l.setdefault(l, [np.zeros_like(T), np.zeros_like(T), np.zeros_like(T)])
+            gr += a * Y
+            gt += -a / (l + 1) * (Yp - Ym) / (2.0 * dtheta)
+            gp += -a / (l + 1) * _dphi_real_sh(l, m, T, P) / np.sin(T)
+        R = rc[:, None, None]
+        br = np.zeros((n_r, n_theta, n_phi))
+        bt = np.zeros_like(br)
+        bp = np.zeros_like(br)
+        for l, (gr, gt, gp) in by_l.items():
+            f = R ** (-(l + 2))
+            br += f * gr[None]
+            bt += f * gt[None]
+            bp += f * gp[None]
+        st, ct, sp, cp = np.sin(T), np.cos(T), np.sin(P), np.cos(P)
+        W[4] += br * (st * cp)[None] + bt * (ct * cp)[None] - bp * sp[None]
+        W[5] += br * (st * sp)[None] + bt * (ct * sp)[None] + bp * cp[None]
+        W[6] += br * ct[None] - bt * st[None]
+    if efree:
+        rc, tc, pc = cell_centres(n_r, n_theta, n_phi, r_in, r_out)
+        R3, T3, P3 = np.meshgrid(rc, tc, pc, indexing="ij")
+        v = np.sqrt(W[1] ** 2 + W[2] ** 2 + W[3] ** 2)
+        bmag = np.sqrt(W[4] ** 2 + W[5] ** 2 + W[6] ** 2)
+        brad = W[4] * np.sin(T3) * np.cos(P3) + W[5] * np.sin(T3) * np.sin(P3) + W[6] * np.cos(T3)
+        f = v * np.where(brad < 0.0, -1.0, 1.0) / bmag
+        W[1], W[2], W[3] = f * W[4], f * W[5], f * W[6]
+    info = dict(info, W=W)
+    return prim_to_cons(W, gamma), info
+
+
+def _dphi_real_sh(l, m, theta, phi):
+    """d/dphi of the orthonormal real harmonic Y_lm of ``real_sh``."""
+    if m == 0:
+        return np.zeros_like(theta)
+    P = _normalised_legendre(l, np.cos(theta))[l][abs(m)]
+    if m > 0:
+        return -m * math.sqrt(2.0) * P * np.sin(m * phi)
+    return -m * math.sqrt(2.0) * P * np.cos(-m * phi)
+
+
 def _magnetogram_scale(n_theta, n_phi, lmax, seed, target_max):
     """The factor s of magnetogram(): max |cos(theta) + s f| = target_max."""
     _, tc, pc = cell_centres(2, n_theta, n_phi)
@@ -325,8 +393,15 @@ def ensemble_members(n=32, seed=5):
     return [((int(nr[m]),) + choices[int(ang[m])], m) for m in range(n)]
 
 
-def ensemble_member(shape, mseed):
-    """Parker wind + dipole background and the member's magnetogram."""
-    U, info = background(*shape)
-    Br = magnetogram(shape[1], shape[2], seed=mseed, lmax=min(15, shape[1] // 2))
+def ensemble_member(shape, mseed, start="potential"):
+    """The member's initial state and magnetogram (l <= min(15, N_theta / 2),
+    max |B_r| = 5): Parker wind with the potential field of that magnetogram
+    (``start="potential"``, the time-marching start) or with the dipole alone
+    (``start="dipole"``)."""
+    lmax = min(15, shape[1] // 2)
+    Br = magnetogram(shape[1], shape[2], seed=mseed, lmax=lmax)
+    if start == "potential":
+        U, info = potential_background(*shape, lmax=lmax, seed=mseed)
+    else:
+        U, info = background(*shape)
     return U, Br, info["p_b"]

@@ -352,8 +352,10 @@ typedef struct crn_ensemble crn_ensemble;
 int crn_ensemble_create(crn_grid* const* grids, int32_t n, crn_ensemble** out);
 int crn_ensemble_destroy(crn_ensemble* e);
 
-/* Radial planes per work item for every member; 0 (default) uses each
- * member's own choice (the one its crn_residual uses). */
+/* Radial planes per work item for every member (their tile shapes are kept);
+ * 0 (default) uses each member's own choice (the one its crn_residual uses).
+ * crn_ensemble_kchunk returns the last value set for all members, or after
+ * crn_ensemble_autotune the chunk of its largest size class. */
 int crn_ensemble_set_kchunk(crn_ensemble* e, int32_t kchunk);
 int32_t crn_ensemble_kchunk(const crn_ensemble* e);
 
@@ -370,13 +372,28 @@ int crn_ensemble_residual(crn_ensemble* e, const void* const* U_dev, void* const
 int crn_ensemble_pseudo_time_step(crn_ensemble* e, double* const* U64_dev, int32_t nsteps, double cfl,
                                   double* res_log10_dev, void* stream);
 
-/* Tile autotuner: times the ensemble residual (one warm-up, three timed
- * launches, CUDA events) for the members' own radial chunks and for 4, 6, 8,
- * 12, 16, 24, 32, 48 planes per item, keeps the fastest (set as with
- * crn_ensemble_set_kchunk) and returns it in *kchunk_out.  Synchronises
- * `stream`; R_dev is overwritten. */
+/* Tile autotuner.  Members are grouped in size classes (equal n_theta and
+ * n_phi).  For each class it times the persistent launch over that class's
+ * members alone (one warm-up, three timed launches, CUDA events) for each tile
+ * shape (8 x 32 and 16 x 16 (theta, phi) columns per CTA) and each radial chunk
+ * (the members' own, 4, 6, 8, 12, 16, 24, 32, 48 planes per item), and keeps
+ * the fastest pair for the class's members (crn_ensemble_member_config reads
+ * it back).  *kchunk_out receives the chunk chosen for the class with the most
+ * cells.  R is the same for every tile shape and chunk up to rounding (the
+ * first r face of a chunk is evaluated on the CTA's preamble path).
+ * Synchronises `stream`; R_dev is overwritten. */
 int crn_ensemble_autotune(crn_ensemble* e, const void* const* U_dev, void* const* R_dev, void* stream,
                           int32_t* kchunk_out);
+
+/* Tile shape (0: 8 x 32, 1: 16 x 16 (theta, phi) columns per CTA) and radial
+ * chunk (planes per work item; 0 = the member's own single-launch chunk) of
+ * member m in the persistent launch.  CRN_E_ARG for an index, shape or chunk
+ * out of range; a chunk that gives a member more work items than its
+ * reduction scratch holds is rejected by the next residual call. */
+int crn_ensemble_set_member_config(crn_ensemble* e, int32_t m, int32_t tile, int32_t kchunk);
+
+/* The tile shape and radial chunk (in planes, resolved) member m runs with. */
+int crn_ensemble_member_config(const crn_ensemble* e, int32_t m, int32_t* tile, int32_t* kchunk);
 
 /* Kernel launches issued by the last call of the ensemble. */
 int32_t crn_ensemble_launch_count(const crn_ensemble* e);

@@ -133,6 +133,8 @@ def load_library(build_if_needed: bool = True):
             "crn_ensemble_destroy": (ctypes.c_int, [vp]),
             "crn_ensemble_set_kchunk": (ctypes.c_int, [vp, i32]),
             "crn_ensemble_kchunk": (i32, [vp]),
+            "crn_ensemble_set_member_config": (ctypes.c_int, [vp, i32, i32, i32]),
+            "crn_ensemble_member_config": (ctypes.c_int, [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
             "crn_ensemble_launch_count": (i32, [vp]),
             "crn_ensemble_residual": (ctypes.c_int, [vp, vp, vp, vp, vp, vp]),
             "crn_ensemble_pseudo_time_step": (ctypes.c_int, [vp, vp, i32, dbl, vp, vp]),
@@ -511,6 +513,19 @@ class Ensemble:
     @property
     def last_launch_count(self):
         return int(_lib.crn_ensemble_launch_count(self._h))
+
+    TILES = {0: (8, 32), 1: (16, 16)}
+
+    def member_config(self, m):
+        """(tile shape (theta, phi), radial chunk) member m runs with."""
+        t, k = ctypes.c_int32(), ctypes.c_int32()
+        _check(_lib.crn_ensemble_member_config(self._h, int(m), ctypes.byref(t), ctypes.byref(k)))
+        return self.TILES[t.value], k.value
+
+    def set_member_config(self, m, tile=(8, 32), kchunk=0):
+        """Tile shape ((8, 32) or (16, 16)) and radial chunk (0: the member's own) of member m."""
+        code = {v: c for c, v in self.TILES.items()}[tuple(tile)]
+        _check(_lib.crn_ensemble_set_member_config(self._h, int(m), code, int(kchunk)))
 
     def _check_states(self, Us, name, dtype=None):
         if len(Us) != len(self.grids):

@@ -82,14 +82,20 @@ size_t vjp_scratch_bytes(const crn_grid* g);
 // ensemble records (EnsMember<T> of residual.cuh, opaque here) and launches
 size_t ens_member_bytes_fp64();
 size_t ens_member_bytes_fp32();
-int ens_fill_fp64(crn_grid* g, const void* U, void* R, int kchunk, int item0, double* nu, double* du, void* dst);
-int ens_fill_fp32(crn_grid* g, const void* U, void* R, int kchunk, int item0, double* nu, double* du, void* dst);
+// tile: the member's (theta, phi) tile shape, 0: 8 x 32, 1: 16 x 16
+int ens_fill_fp64(crn_grid* g, const void* U, void* R, int kchunk, int item0, double* nu, double* du, int tile,
+                  void* dst);
+int ens_fill_fp32(crn_grid* g, const void* U, void* R, int kchunk, int item0, double* nu, double* du, int tile,
+                  void* dst);
+// work items of a member for a tile shape and radial chunk
+int ens_member_items(const crn_grid* g, int tile, int kchunk);
+// the persistent launch over `nmem` member records of one tile shape
 cudaError_t launch_ensemble_fp64(const void* dev, int nmem, int nitems, unsigned int* next, int limiter,
-                                 int nctas, cudaStream_t st);
+                                 int tile, int nctas, cudaStream_t st);
 cudaError_t launch_ensemble_fp32(const void* dev, int nmem, int nitems, unsigned int* next, int limiter,
-                                 int nctas, cudaStream_t st);
-int ensemble_ctas_per_sm_fp64(int limiter);
-int ensemble_ctas_per_sm_fp32(int limiter);
+                                 int tile, int nctas, cudaStream_t st);
+int ensemble_ctas_per_sm_fp64(int limiter, int tile);
+int ensemble_ctas_per_sm_fp32(int limiter, int tile);
 cudaError_t launch_ensemble_update(const void* dev, int nmem, int nitems, double cfl, bool fp32,
                                    cudaStream_t st);
 size_t ens_update_bytes();

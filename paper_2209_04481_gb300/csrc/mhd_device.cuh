@@ -65,6 +65,12 @@ struct Shape {
   int64_t ncell;
 };
 
+// (theta, phi) tile shapes of the ensemble kernel, all of 256 threads:
+// tile t has ens_tt(t) x ens_tp(t) columns per CTA
+constexpr int kEnsTileCount = 2;
+__host__ __device__ constexpr int ens_tt(int t) { return t == 0 ? 8 : 16; }
+__host__ __device__ constexpr int ens_tp(int t) { return t == 0 ? 32 : 16; }
+
 template <class T> __device__ __forceinline__ T frcp(T x);
 template <> __device__ __forceinline__ double frcp<double>(double x) { return 1.0 / x; }
 template <> __device__ __forceinline__ float frcp<float>(float x) { return __fdividef(1.0f, x); }

@@ -847,8 +847,10 @@ residual_tiled(Shape sh, Geo<T> g, Phys<T> ph, const double* __restrict__ Br,
 // member by member; CTAs take items from a global counter (zeroed before the
 // launch) until none are left.  Each member keeps its own reduction scratch,
 // so its norms and dtmin come out exactly as from its own launch with the
-// same radial chunk.
+// same radial chunk.  The kernel is instantiated per (theta, phi) tile shape;
+// members with another shape go to that shape's launch.
 // ---------------------------------------------------------------------------
+
 template <class T>
 struct EnsMember {
   Shape sh;
@@ -858,8 +860,9 @@ struct EnsMember {
   const T* U;
   T* R;
   Reduce red;
-  int kchunk, ntiles, nitems, item0;
+  int kchunk, ntiles, nitems, item0, tile;
 };
+
 
 template <class T, int LIM, int TT, int TP>
 __global__ void __launch_bounds__(TT * TP, MinCtas<T>::value)

@@ -128,14 +128,17 @@ cudaError_t launch_efield_fp32(crn_grid* g, const float* U, double* E, bool volu
   return efield_t<float>(g, U, E, volume, st, nl);
 }
 size_t ens_member_bytes_fp32() { return sizeof(EnsMember<float>); }
-int ens_fill_fp32(crn_grid* g, const void* U, void* R, int kchunk, int item0, double* nu, double* du, void* dst) {
+int ens_member_items(const crn_grid* g, int tile, int kchunk) { return ens_items(g, tile, kchunk); }
+int ens_fill_fp32(crn_grid* g, const void* U, void* R, int kchunk, int item0, double* nu, double* du, int tile,
+                 void* dst) {
   EnsMember<float>* m = static_cast<EnsMember<float>*>(dst);
-  ens_fill_t<float>(g, static_cast<const float*>(U), static_cast<float*>(R), kchunk, item0, nu, du, m);
+  ens_fill_t<float>(g, static_cast<const float*>(U), static_cast<float*>(R), kchunk, item0, nu, du, tile, m);
   return m->nitems;
 }
 cudaError_t launch_ensemble_fp32(const void* dev, int nmem, int nitems, unsigned int* next, int limiter,
-                                  int nctas, cudaStream_t st) {
-  return launch_ensemble_t<float>(static_cast<const EnsMember<float>*>(dev), nmem, nitems, next, limiter, nctas, st);
+                                  int tile, int nctas, cudaStream_t st) {
+  return launch_ensemble_t<float>(static_cast<const EnsMember<float>*>(dev), nmem, nitems, next, limiter, tile, nctas,
+                                st);
 }
-int ensemble_ctas_per_sm_fp32(int limiter) { return ensemble_ctas_t<float>(limiter); }
+int ensemble_ctas_per_sm_fp32(int limiter, int tile) { return ensemble_ctas_t<float>(limiter, tile); }
 }  // namespace crn

@@ -15,14 +15,16 @@ cudaError_t launch_efield_fp64(crn_grid* g, const double* U, double* E, bool vol
   return efield_t<double>(g, U, E, volume, st, nl);
 }
 size_t ens_member_bytes_fp64() { return sizeof(EnsMember<double>); }
-int ens_fill_fp64(crn_grid* g, const void* U, void* R, int kchunk, int item0, double* nu, double* du, void* dst) {
+int ens_fill_fp64(crn_grid* g, const void* U, void* R, int kchunk, int item0, double* nu, double* du, int tile,
+                 void* dst) {
   EnsMember<double>* m = static_cast<EnsMember<double>*>(dst);
-  ens_fill_t<double>(g, static_cast<const double*>(U), static_cast<double*>(R), kchunk, item0, nu, du, m);
+  ens_fill_t<double>(g, static_cast<const double*>(U), static_cast<double*>(R), kchunk, item0, nu, du, tile, m);
   return m->nitems;
 }
 cudaError_t launch_ensemble_fp64(const void* dev, int nmem, int nitems, unsigned int* next, int limiter,
-                                  int nctas, cudaStream_t st) {
-  return launch_ensemble_t<double>(static_cast<const EnsMember<double>*>(dev), nmem, nitems, next, limiter, nctas, st);
+                                  int tile, int nctas, cudaStream_t st) {
+  return launch_ensemble_t<double>(static_cast<const EnsMember<double>*>(dev), nmem, nitems, next, limiter, tile, nctas,
+                                st);
 }
-int ensemble_ctas_per_sm_fp64(int limiter) { return ensemble_ctas_t<double>(limiter); }
+int ensemble_ctas_per_sm_fp64(int limiter, int tile) { return ensemble_ctas_t<double>(limiter, tile); }
 }  // namespace crn

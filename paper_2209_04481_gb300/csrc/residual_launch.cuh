@@ -112,8 +112,8 @@ cudaError_t efield_t(crn_grid* g, const T* U, double* E, bool volume, cudaStream
 // ---- ensemble: member records and the persistent launch
 template <class T>
 void ens_fill_t(crn_grid* g, const T* U, T* R, int kchunk, int item0, double* norms_user, double* dt_user,
-                EnsMember<T>* m) {
-  constexpr int TT = TileFor<T>::TT, TP = TileFor<T>::TP;
+                int tile, EnsMember<T>* m) {
+  const int TT = ens_tt(tile), TP = ens_tp(tile);
   m->sh = g->shape;
   m->g = geo_of<T>(g);
   m->ph = phys_of<T>(g);
@@ -125,12 +125,12 @@ void ens_fill_t(crn_grid* g, const T* U, T* R, int kchunk, int item0, double* no
   m->ntiles = ((g->shape.nt + TT - 1) / TT) * ((g->shape.np + TP - 1) / TP);
   m->nitems = m->ntiles * ((g->shape.nr + kchunk - 1) / kchunk);
   m->item0 = item0;
+  m->tile = tile;
 }
 
-template <class T>
-cudaError_t launch_ensemble_t(const EnsMember<T>* dev, int nmem, int nitems, unsigned int* next, int limiter,
-                              int nctas, cudaStream_t st) {
-  constexpr int TT = TileFor<T>::TT, TP = TileFor<T>::TP;
+template <class T, int TT, int TP>
+cudaError_t launch_ensemble_shape(const EnsMember<T>* dev, int nmem, int nitems, unsigned int* next, int limiter,
+                                  int nctas, cudaStream_t st) {
   const size_t smem = TileDims<TT, TP>::template smem_bytes<T>();
   cudaError_t e = cudaMemsetAsync(next, 0, sizeof(unsigned int), st);
   if (e != cudaSuccess) return e;
@@ -143,10 +143,16 @@ cudaError_t launch_ensemble_t(const EnsMember<T>* dev, int nmem, int nitems, uns
   return cudaGetLastError();
 }
 
-// shared-memory opt-in and resident CTAs per SM of the ensemble kernel
+// the persistent launch over the members of one tile shape
 template <class T>
-int ensemble_ctas_t(int limiter) {
-  constexpr int TT = TileFor<T>::TT, TP = TileFor<T>::TP;
+cudaError_t launch_ensemble_t(const EnsMember<T>* dev, int nmem, int nitems, unsigned int* next, int limiter,
+                              int tile, int nctas, cudaStream_t st) {
+  if (tile == 0) return launch_ensemble_shape<T, ens_tt(0), ens_tp(0)>(dev, nmem, nitems, next, limiter, nctas, st);
+  return launch_ensemble_shape<T, ens_tt(1), ens_tp(1)>(dev, nmem, nitems, next, limiter, nctas, st);
+}
+
+template <class T, int TT, int TP>
+int ensemble_ctas_shape(int limiter) {
   const int smem = (int)TileDims<TT, TP>::template smem_bytes<T>();
   auto setup = [&](auto kern) {
     int n = 0;
@@ -157,6 +163,19 @@ int ensemble_ctas_t(int limiter) {
   if (limiter == CRN_LIM_NONE) return setup(residual_ensemble<T, 0, TT, TP>);
   if (limiter == CRN_LIM_MINMOD) return setup(residual_ensemble<T, 1, TT, TP>);
   return setup(residual_ensemble<T, 2, TT, TP>);
+}
+
+// shared-memory opt-in and resident CTAs per SM of one tile shape's kernel
+template <class T>
+int ensemble_ctas_t(int limiter, int tile) {
+  return tile == 0 ? ensemble_ctas_shape<T, ens_tt(0), ens_tp(0)>(limiter)
+                   : ensemble_ctas_shape<T, ens_tt(1), ens_tp(1)>(limiter);
+}
+
+// work items of one member for a tile shape and radial chunk
+inline int ens_items(const crn_grid* g, int tile, int kchunk) {
+  const int TT = ens_tt(tile), TP = ens_tp(tile);
+  return ((g->shape.nt + TT - 1) / TT) * ((g->shape.np + TP - 1) / TP) * ((g->shape.nr + kchunk - 1) / kchunk);
 }
 
 template <class T>

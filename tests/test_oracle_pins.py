@@ -730,3 +730,44 @@ def test_glm_damping_source():
     _, dR = oracle.residual_jvp(g, U, None, dU, None)
     np.testing.assert_allclose(dR[8], -0.7, rtol=1e-14)
     assert np.abs(dR[:8]).max() < 1e-13
+
+
+def test_potential_background_is_the_magnetogram_potential_field():
+    """The time-marching start: B = -grad Phi of the magnetogram's potential
+    Phi = cos(theta)/(2 r^2) + s sum a_lm r^-(l+1) Y_lm / (l + 1).  Checked
+    against central differences of Phi itself (built here from the same
+    seeded coefficients), B_r at r = 1 against the magnetogram, and the
+    dipole-only case against the plain Parker + dipole background."""
+    nr, nt, npp, lmax, seed = 6, 8, 16, 4, 7
+    U, info = ci.potential_background(nr, nt, npp, lmax=lmax, seed=seed)
+    Ud, _ = ci.potential_background(nr, nt, npp, lmax=lmax, seed=seed, dipole_only=True)
+    np.testing.assert_array_equal(Ud, ci.background(nr, nt, npp)[0])
+    s = ci._magnetogram_scale(nt, npp, lmax, seed, 5.0)
+
+    def phi(r, t, p):
+        rng = np.random.default_rng(seed)
+        out = np.cos(t) / (2.0 * r ** 2)
+        for (l, m, Y) in ci.real_sh(lmax, t, p):
+            if l == 0:
+                continue
+            out = out + s * rng.standard_normal() / l * r ** (-(l + 1)) * Y / (l + 1)
+        return out
+
+    rc, tc, pc = ci.cell_centres(nr, nt, npp)
+    R, T, P = np.meshgrid(rc, tc, pc, indexing="ij")
+    h = 1e-5
+    br = -(phi(R + h, T, P) - phi(R - h, T, P)) / (2 * h)
+    bt = -(phi(R, T + h, P) - phi(R, T - h, P)) / (2 * h) / R
+    bp = -(phi(R, T, P + h) - phi(R, T, P - h)) / (2 * h) / (R * np.sin(T))
+    W = info["W"]
+    er = np.stack([np.sin(T) * np.cos(P), np.sin(T) * np.sin(P), np.cos(T)])
+    et = np.stack([np.cos(T) * np.cos(P), np.cos(T) * np.sin(P), -np.sin(T)])
+    ep = np.stack([-np.sin(P), np.cos(P), np.zeros_like(P)])
+    B = W[4:7]
+    for comp, ref in ((er, br), (et, bt), (ep, bp)):
+        np.testing.assert_allclose(np.einsum("cijk,cijk->ijk", B, comp), ref, atol=1e-7 * np.abs(ref).max())
+    # at r = 1 the radial component is the prescribed magnetogram
+    _, tb, pb = ci.cell_centres(2, nt, npp)
+    T2, P2 = np.meshgrid(tb, pb, indexing="ij")
+    br1 = -(phi(1.0 + h, T2, P2) - phi(1.0 - h, T2, P2)) / (2 * h)
+    np.testing.assert_allclose(br1, ci.magnetogram(nt, npp, lmax=lmax, seed=seed), atol=1e-7)
