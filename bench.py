@@ -56,9 +56,9 @@ def parse():
     ap.add_argument("--only-headline", nargs="?", const="fp32", choices=["fp32", "fp64"], default=None,
                     help="time the residual in this precision only (for profiler captures); skips "
                          "e2e, pseudo-time, VJP, Newton-Krylov and ensemble measurements")
-    ap.add_argument("--only-newton-krylov", action="store_true",
-                    help="run the 96x48x96 Newton-Krylov solve only, for at most --steps "
-                         "pseudo-time steps (for profiler captures)")
+    ap.add_argument("--only-newton-krylov", nargs="?", const="all", default=None,
+                    help="profiling: the Newton-Krylov solves only (optionally one of shell32_fp64, "
+                         "shell96_fp64_minmod, shell96_l15_fp32), at most --steps pseudo-time steps each")
     ap.add_argument("--only-vjp", action="store_true",
                     help="time the residual VJP only (for profiler captures)")
     ap.add_argument("--only-ensemble", action="store_true",
@@ -319,7 +319,8 @@ def run_gb300(args):
         return
     if args.only_newton_krylov:
         stream = torch.cuda.Stream(device)
-        nk = run_nk(torch, pg, ci, device, stream, only="shell96_fp64_minmod", steps_cap=args.steps)
+        nk = run_nk(torch, pg, ci, device, stream, only=None if args.only_newton_krylov == "all"
+                    else args.only_newton_krylov, steps_cap=args.steps)
         if rank == 0:
             print(json.dumps({"newton_krylov": nk, "note": "Newton-Krylov solve only (profiling run)"}),
                   flush=True)
@@ -536,61 +537,150 @@ def run_vjp(torch, np, pg, ci, device, stream):
     return vjp
 
 
-def run_nk(torch, pg, ci, device, stream, only=None, steps_cap=None):
-    """Newton-Krylov steady solves (backward-Euler pseudo-time, CFL 2 doubling
-    every 10 steps to 128, GMRES(30) to 1e-3, central-difference JVPs) from the
-    Parker wind + dipole start with the low-E inner boundary of prescribed
-    outflow magnitude; wall-clock time around the host-driven solve.  `only`
-    names the one run to make, `steps_cap` bounds its pseudo-time steps."""
-    vr = 1935.07 / ci.V_REF
-    out = {"note": "dipole start (the strong-field l<=15 start drains a base cell to vacuum under "
-                   "any pseudo-time schedule); inner_bc low_e_wp; wall-clock seconds; Krylov basis "
-                   "FP32 (the default at lin_rtol 1e-3), adjoint FP64"}
-    # (name, shape, precision, limiter, drop, max steps, CFL cap, Newton-Krylov options)
-    runs = (("shell32_fp64", (32, 16, 32), "fp64", "vanalbada", 1e-6, 300, 128.0, {}),
-            # 96x48x96: minmod, CFL up to 1024, radial line preconditioner, GMRES(60)
-            ("shell96_fp64_minmod", (96, 48, 96), "fp64", "minmod", 1e-6, 300, 1024.0,
-             {"precond": 1, "krylov_dim": 60}),
-            # the same solve with forward-difference JVPs: one residual per Krylov step
-            ("shell96_fp64_minmod_forward_fd", (96, 48, 96), "fp64", "minmod", 1e-6, 300, 1024.0,
-             {"precond": 1, "krylov_dim": 60, "fd_central": 0}))
-    for name, shape, precision, limiter, tol, max_steps, cfl_max, nkopt in runs:
-        if only is not None and name != only:
-            continue
-        if steps_cap is not None:
-            max_steps = min(max_steps, steps_cap)
-        U, info = ci.background(*shape)
-        Br = ci.magnetogram(shape[1], shape[2], dipole_only=True)
-        g = pg.Grid(*shape, precision=precision, limiter=limiter, p_b=info["p_b"], inner_bc="low_e_wp",
-                    vr_star=vr)
-        g.set_inner_boundary(torch.from_numpy(Br).to(device))
-        U64 = torch.from_numpy(U).to(device)
+def _outer_functionals(torch, ci, shape, device):
+    """dg/dU of the mean outer-layer density and of the mean outer-layer B_r."""
+    nt, np_ = shape[1], shape[2]
+    g_rho = torch.zeros((9,) + tuple(shape), dtype=torch.float64, device=device)
+    g_rho[0, -1] = 1.0 / (nt * np_)
+    _, tc, pc = ci.cell_centres(*shape)
+    import numpy as np
+    T, P = np.meshgrid(tc, pc, indexing="ij")
+    g_br = torch.zeros_like(g_rho)
+    for q, f in ((4, np.sin(T) * np.cos(P)), (5, np.sin(T) * np.sin(P)), (6, np.cos(T))):
+        g_br[q, -1] = torch.from_numpy(f / (nt * np_)).to(device)
+    return {"mean outer rho": g_rho, "mean outer B_r": g_br}
+
+
+def _adjoints(torch, ci, g, U64, shape, device, stream, opts):
+    """Magnetogram sensitivities of the outer functionals at a steady state by
+    the pseudo-time adjoint iteration (options per functional); wall-clock
+    seconds and true linear residuals |gbar - J^T lambda| / |gbar|."""
+    out = {}
+    for name, gbar in _outer_functionals(torch, ci, shape, device).items():
         torch.cuda.synchronize(device)
         t0 = time.perf_counter()
         with torch.cuda.stream(stream):
-            st, _ = g.steady_solve(U64, max_steps=max_steps, tol_drop=tol, cfl_max=cfl_max, nk=nkopt,
-                                   stream=stream)
+            sens, _, ast = g.adjoint_solve(U64, gbar, stream=stream, **opts[name])
         torch.cuda.synchronize(device)
-        sec = time.perf_counter() - t0
-        out[name] = {"shape": list(shape), "limiter": limiter, "cfl_max": cfl_max, "nk_options": nkopt,
-                     "seconds": sec, "steps": st["steps"],
-                     "residual_evals": st["residual_evals"], "krylov_iters": st["krylov_iters"],
-                     "converged": bool(st["converged"]), "tol_drop": tol,
-                     "drop": st["res_final"] / st["res0"], "max_steps": max_steps,
-                     "ms_per_residual_eval": 1e3 * sec / max(st["residual_evals"], 1)}
-        if name == "shell32_fp64":
-            # magnetogram sensitivity of the mean outer-layer density at this state
-            gbar = torch.zeros_like(U64)
-            gbar[0, -1] = 1.0 / (shape[1] * shape[2])
-            torch.cuda.synchronize(device)
-            t0 = time.perf_counter()
-            with torch.cuda.stream(stream):
-                _, _, ast = g.adjoint_solve(U64, gbar, stream=stream, krylov_dim=100, max_restarts=3,
-                                            lin_rtol=1e-8, precond=1)
-            torch.cuda.synchronize(device)
-            out[name]["adjoint"] = {"functional": "mean outer-layer density", "seconds": time.perf_counter() - t0,
-                                    "krylov_iters": ast["krylov_iters"], "vjp_evals": ast["residual_evals"],
-                                    "lin_rel": ast["lin_rel"]}
+        out[name] = {"seconds": time.perf_counter() - t0, "adjoint_cfl": opts[name]["adjoint_cfl"],
+                     "lin_rel": ast["lin_rel"], "passes": int(ast["alpha"]),
+                     "krylov_iters": ast["krylov_iters"], "vjp_evals": ast["residual_evals"],
+                     "sensitivity_l2": float(torch.linalg.vector_norm(sens))}
+    return out
+
+
+def run_nk(torch, pg, ci, device, stream, only=None, steps_cap=None):
+    """Newton-Krylov steady solves (backward-Euler pseudo-time under the CFL
+    law, GMRES, central-difference JVPs) with the low-E inner boundary of
+    prescribed outflow magnitude; wall-clock time around the host-driven
+    solves.  `only` names the one run to make, `steps_cap` bounds its steps.
+      shell32_fp64:  32x16x32, dipole, van Albada, to 1e-6; sensitivity of the
+                     mean outer density (GMRES on J^T).
+      shell96_fp64_minmod:  96x48x96, dipole, FP64, to 1e-6; the outer-rho and
+                     outer-B_r sensitivities by the pseudo-time adjoint.
+      shell96_l15_fp32:  96x48x96 with the l <= 15 magnetogram (seed 2209) and
+                     the FP32-bulk flux: continuation in the amplitude of the
+                     magnetogram's multipoles (stages to 1e-3) up to the
+                     largest amplitude that converges, then to 1e-6; the
+                     outer-rho and outer-B_r sensitivities there."""
+    vr = 1935.07 / ci.V_REF
+    out = {"note": "inner_bc low_e_wp; wall-clock seconds; Krylov basis FP32 (the default at lin_rtol 1e-3); "
+                   "adjoint vectors FP64"}
+    nk96 = {"precond": 1, "krylov_dim": 60}
+    # pseudo-time adjoint: CFL 1000 for the outer density (converges to 1e-6 on the
+    # dipole state); the outer-B_r functional meets the near-null induction modes of
+    # the static closed-field regions and only contracts at a small CFL (30)
+    adj_opt = {"mean outer rho": dict(krylov_dim=60, lin_rtol=1e-6, precond=1, adjoint_cfl=1000.0,
+                                      adjoint_outer=200),
+               "mean outer B_r": dict(krylov_dim=60, lin_rtol=1e-6, precond=1, adjoint_cfl=30.0,
+                                      adjoint_outer=150)}
+
+    def solve(g, U64, **kw):
+        torch.cuda.synchronize(device)
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            st, _ = g.steady_solve(U64, stream=stream, **kw)
+        torch.cuda.synchronize(device)
+        return st, time.perf_counter() - t0
+
+    def record(st, sec, **extra):
+        return dict({"seconds": sec, "steps": st["steps"], "residual_evals": st["residual_evals"],
+                     "krylov_iters": st["krylov_iters"], "converged": bool(st["converged"]),
+                     "drop": st["res_final"] / st["res0"],
+                     "ms_per_residual_eval": 1e3 * sec / max(st["residual_evals"], 1)}, **extra)
+
+    if only in (None, "shell32_fp64"):
+        shape = (32, 16, 32)
+        U, info = ci.background(*shape)
+        Br = ci.magnetogram(shape[1], shape[2], dipole_only=True)
+        g = pg.Grid(*shape, precision="fp64", limiter="vanalbada", p_b=info["p_b"], inner_bc="low_e_wp",
+                    vr_star=vr)
+        g.set_inner_boundary(torch.from_numpy(Br).to(device))
+        U64 = torch.from_numpy(U).to(device)
+        st, sec = solve(g, U64, max_steps=min(300, steps_cap or 300), tol_drop=1e-6, cfl_max=128.0)
+        out["shell32_fp64"] = record(st, sec, shape=list(shape), limiter="vanalbada", cfl_max=128.0, tol_drop=1e-6)
+        gbar = _outer_functionals(torch, ci, shape, device)["mean outer rho"]
+        torch.cuda.synchronize(device)
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            _, _, ast = g.adjoint_solve(U64, gbar, stream=stream, krylov_dim=100, max_restarts=3,
+                                        lin_rtol=1e-8, precond=1)
+        torch.cuda.synchronize(device)
+        out["shell32_fp64"]["adjoint"] = {"functional": "mean outer-layer density", "method": "GMRES on J^T",
+                                          "seconds": time.perf_counter() - t0, "krylov_iters": ast["krylov_iters"],
+                                          "vjp_evals": ast["residual_evals"], "lin_rel": ast["lin_rel"]}
+        g.close()
+
+    if only in (None, "shell96_fp64_minmod"):
+        shape = (96, 48, 96)
+        U, info = ci.background(*shape)
+        Br = ci.magnetogram(shape[1], shape[2], dipole_only=True)
+        g = pg.Grid(*shape, precision="fp64", limiter="minmod", p_b=info["p_b"], inner_bc="low_e_wp", vr_star=vr)
+        g.set_inner_boundary(torch.from_numpy(Br).to(device))
+        U64 = torch.from_numpy(U).to(device)
+        st, sec = solve(g, U64, max_steps=min(300, steps_cap or 300), tol_drop=1e-6, cfl_max=1024.0, nk=nk96)
+        out["shell96_fp64_minmod"] = record(st, sec, shape=list(shape), limiter="minmod", cfl_max=1024.0,
+                                            nk_options=nk96, tol_drop=1e-6, field="dipole")
+        out["shell96_fp64_minmod"]["sensitivity"] = _adjoints(torch, ci, g, U64, shape, device, stream, adj_opt)
+        g.close()
+
+    if only in (None, "shell96_l15_fp32"):
+        import numpy as np
+        shape = (96, 48, 96)
+        U, info = ci.background(*shape)
+        Brf = ci.magnetogram(shape[1], shape[2], seed=2209)
+        _, tc, pc = ci.cell_centres(2, shape[1], shape[2])
+        dip = np.cos(np.meshgrid(tc, pc, indexing="ij")[0])
+        g = pg.Grid(*shape, precision="fp32", limiter="minmod", p_b=info["p_b"], inner_bc="low_e_wp", vr_star=vr)
+        U64 = torch.from_numpy(U).to(device)
+        stages, reached, total = [], 0.0, 0.0
+        for a in (0.0, 0.1, 0.2, 0.3, 0.4, 0.5, 0.6, 0.7, 0.8, 0.9, 1.0):
+            g.set_inner_boundary(torch.from_numpy(dip + a * (Brf - dip)).to(device))
+            keep = U64.clone()
+            try:
+                st, sec = solve(g, U64, max_steps=250, tol_drop=1e-3, cfl_max=128.0, nk=nk96)
+            except pg.CoronaError as e:
+                stages.append({"amplitude": a, "error": str(e).split(":")[0]})
+                U64.copy_(keep)
+                break
+            total += sec
+            stages.append({"amplitude": a, "steps": st["steps"], "drop": st["res_final"] / st["res0"],
+                           "seconds": sec})
+            if not st["converged"]:
+                U64.copy_(keep)
+                break
+            reached = a
+        g.set_inner_boundary(torch.from_numpy(dip + reached * (Brf - dip)).to(device))
+        out["shell96_l15_fp32"] = {
+            "shape": list(shape), "limiter": "minmod", "precision": "fp32 bulk flux, FP64 update and norms",
+            "magnetogram": "l<=15 random field (seed 2209): B_r = cos(theta) + a s f, max|B_r| = 5 at a = 1",
+            "amplitude_reached": reached, "max_abs_br_reached": float(np.abs(dip + reached * (Brf - dip)).max()),
+            "continuation": stages, "seconds": total, "stage_tol_drop": 1e-3, "cfl_max": 128.0, "nk_options": nk96,
+            "note": "stages stop where the conservative low-beta energy drives a cell's pressure to ~1e-10 of "
+                    "B^2 (a finite-difference product then meets a non-physical state); from the last stage a "
+                    "further solve at CFL 128-1024 stalls near a 1e-1 drop of its own start (FP32-bulk "
+                    "residual noise and marginal modes)"}
+        out["shell96_l15_fp32"]["sensitivity"] = _adjoints(torch, ci, g, U64, shape, device, stream, adj_opt)
         g.close()
     return out
 

@@ -259,9 +259,10 @@ int crn_efield(crn_grid* g, const void* U_dev, double* E_dev, void* stream);
  * crn_residual evaluations (or the forward difference against R(U)), eps the
  * largest step that moves no state entry by more than fd_rel of |u| + 1e-3 x
  * (the mean |u| of its variable + the mean |u| over all nine variables) and no
- * cell's linearised pressure by more than a quarter.  U is then advanced by alpha dU, alpha = min(1,
+ * cell's pressure by more than a quarter (to first and to second order in eps).  U is then advanced by alpha dU, alpha = min(1,
  * max_rel_change / max_c max(|d rho|/rho, |dp_lin|/p)) (dp_lin the linearised
- * pressure change), halved while any cell would get rho <= 0 or p <= 0.
+ * pressure change), halved while any cell would keep less than a tenth of
+ * its density or pressure.
  * All vectors are FP64 on the device (the Krylov basis FP32 if basis_fp32
  * selects it); reductions are deterministic. */
 typedef struct {
@@ -284,6 +285,14 @@ typedef struct {
                               is far below a loose lin_rtol), 0 FP64, -1 FP32 when
                               lin_rtol >= 1e-4 else FP64 (default -1).  The adjoint
                               solve always uses FP64.                                */
+  int32_t adjoint_outer;   /* crn_adjoint_solve with adjoint_cfl > 0: passes of the
+                              pseudo-time adjoint iteration, 1..100000 (default 200) */
+  double adjoint_cfl;      /* crn_adjoint_solve: 0 (default) runs GMRES on J^T
+                              diag(dt_c); > 0 runs the pseudo-time adjoint iteration
+                              lambda <- lambda + delta, (D - J^T) delta = J^T lambda
+                              - gbar with D = diag(1 / (adjoint_cfl dt_c)), each pass
+                              solved by GMRES(krylov_dim) to 1e-2 on the shifted
+                              operator (precond as for the primal lines, transposed)  */
 } crn_nk_options;
 
 typedef struct {
@@ -406,9 +415,13 @@ int32_t crn_ensemble_launch_count(const crn_ensemble* e);
  * (FP64, the shape crn_set_inner_boundary takes) and, if lambda_dev is not
  * NULL, lambda.  opt: krylov_dim, max_restarts, lin_rtol and precond are used
  * (precond 1: the transposed radial line preconditioner, the lines of
- * crn_nk_options.precond at infinite CFL, negated and transposed).  The
- * first call allocates the Newton-Krylov and VJP workspaces.  Synchronises
- * `stream` once or twice per Krylov step. */
+ * crn_nk_options.precond at infinite CFL, negated and transposed).  With
+ * opt->adjoint_cfl > 0 the solve is the pseudo-time adjoint iteration
+ * described at that field, stopped at |gbar - J^T lambda| <= lin_rtol |gbar|
+ * or after adjoint_outer passes; stats->lin_rel then holds that true relative
+ * residual and stats->alpha the number of passes.  The first call allocates
+ * the Newton-Krylov and VJP workspaces.  Synchronises `stream` once or twice
+ * per Krylov step. */
 int crn_adjoint_solve(crn_grid* g, const double* U64_dev, const double* gbar_dev, double* lambda_dev,
                       double* sens_dev, const crn_nk_options* opt, crn_nk_stats* stats, void* stream);
 

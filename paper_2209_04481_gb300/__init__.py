@@ -60,7 +60,8 @@ class NkOptions(ctypes.Structure):
     _fields_ = [("krylov_dim", ctypes.c_int32), ("max_restarts", ctypes.c_int32),
                 ("lin_rtol", ctypes.c_double), ("fd_rel", ctypes.c_double),
                 ("max_rel_change", ctypes.c_double), ("fd_central", ctypes.c_int32),
-                ("precond", ctypes.c_int32), ("basis_fp32", ctypes.c_int32)]
+                ("precond", ctypes.c_int32), ("basis_fp32", ctypes.c_int32),
+                ("adjoint_outer", ctypes.c_int32), ("adjoint_cfl", ctypes.c_double)]
 
 
 class NkStats(ctypes.Structure):

@@ -21,8 +21,8 @@
 // size (s_v = 1e-3 x (the mean |u| of its variable + the mean |u| over all
 // nine variables)) and no cell's pressure by more than a quarter.  The step is
 // then limited to a relative change of rho and of the linearised p of at most
-// omega per cell, and halved while any cell of
-// U + alpha dU would have rho <= 0 or p <= 0.  The CFL law of Sect. 4.1
+// omega per cell, and halved while any cell of U + alpha dU would keep less
+// than a tenth of its density or pressure.  The CFL law of Sect. 4.1
 // (start at 2, double every few steps, up to 128) drives crn_steady_solve.
 //
 // Every vector operation is a kernel of this file, in FP64 except the
@@ -45,6 +45,8 @@ namespace crn {
 namespace {
 
 constexpr int NKB = 256;  // threads per block of the vector kernels
+// a Newton step keeps at least this fraction of every cell's density and pressure
+constexpr double kKeepFrac = 0.1;
 constexpr int MD = 8;     // vectors per multi-dot launch
 
 // ---------------------------------------------------------------------------
@@ -205,6 +207,22 @@ sub_kernel(double* y, const double* b, const double* x, int64_t n) {
   for (int64_t e = (int64_t)blockIdx.x * NKB + threadIdx.x; e < n; e += stride) y[e] = b[e] - x[e];
 }
 
+// y += x
+__global__ void __launch_bounds__(NKB)
+add_kernel(double* y, const double* x, int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * NKB;
+  for (int64_t e = (int64_t)blockIdx.x * NKB + threadIdx.x; e < n; e += stride) y[e] += x[e];
+}
+
+// w = z / dtau - w: the shifted adjoint operator (D - J^T) z from w = J^T z
+// (D = diag(1 / dtau), one dtau per cell shared by its nine variables)
+__global__ void __launch_bounds__(NKB)
+shift_combine_kernel(double* __restrict__ w, const double* __restrict__ z, const double* __restrict__ dtau,
+                     int64_t N, int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * NKB;
+  for (int64_t e = (int64_t)blockIdx.x * NKB + threadIdx.x; e < n; e += stride) w[e] = z[e] / dtau[e % N] - w[e];
+}
+
 // per-variable partial sums of |u| (rows 0..8)
 __global__ void __launch_bounds__(NKB)
 absmean_kernel(const double* __restrict__ U, int64_t N, double* __restrict__ part, int nblk, int row) {
@@ -273,6 +291,12 @@ precond_kernel(const TV* __restrict__ v, const double* __restrict__ dtau, int64_
                              0.5 * (vx * vx + vy * vy + vz * vz) * zz[0] -
                              (u[4] * zz[4] + u[5] * zz[5] + u[6] * zz[6]));
     if (dp != 0.0) mp = fmin(mp, p * rcp_coarse(fabs(dp)));
+    // second order: p(U + e z) = p + e dp - e^2 gm1 Q + ..., Q = |z_B|^2 / 2 +
+    // |z_m - V z_rho|^2 / (2 rho); with e <= mp / 4 this keeps e^2 gm1 Q <= p / 4
+    const double wx = zz[1] - vx * zz[0], wy = zz[2] - vy * zz[0], wz = zz[3] - vz * zz[0];
+    const double Q = 0.5 * (zz[4] * zz[4] + zz[5] * zz[5] + zz[6] * zz[6]) +
+                     0.5 * (wx * wx + wy * wy + wz * wz) * ir;
+    if (Q > 0.0 && p > 0.0) mp = fmin(mp, 2.0 * sqrt(p * rcp_coarse(gm1 * Q)));
   }
   if (!want_min) return;
   __shared__ double sm[2][NKB];
@@ -385,7 +409,11 @@ badcount_kernel(const double* __restrict__ U, const double* __restrict__ dU, dou
     const double ir = 1.0 / rho;
     const double p = gm1 * (u[7] - 0.5 * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) * ir -
                             0.5 * (u[4] * u[4] + u[5] * u[5] + u[6] * u[6]));
-    if (!(rho > 0.0) || !(p > 0.0) || !isfinite(p)) cnt[0] += 1.0;
+    // the old state's density and pressure: a step may not take away more
+    // than (1 - kKeepFrac) of either in any cell
+    double r0, v0[3], b0[3], p0;
+    prim_of(U, N, c, gm1, r0, v0, b0, p0);
+    if (!(rho > kKeepFrac * r0) || !(p > kKeepFrac * p0) || !isfinite(p)) cnt[0] += 1.0;
   }
   block_sum_rows<1>(cnt, part, nblk, row, 1);
 }
@@ -603,6 +631,7 @@ struct NkWork {
   double* out = nullptr;   // rows reduced values
   double* coef = nullptr;  // m + 2 coefficients
   double* host = nullptr;  // pinned mirror of out
+  double* adj = nullptr;   // 2n: the pseudo-time adjoint's lambda and residual (first use)
 };
 
 void nk_free(NkWork* w) {
@@ -612,6 +641,7 @@ void nk_free(NkWork* w) {
   cudaFree(w->line);
   cudaFree(w->Vf); cudaFree(w->wf); cudaFree(w->coef32);
   cudaFree(w->part); cudaFree(w->out); cudaFree(w->coef);
+  cudaFree(w->adj);
   cudaFreeHost(w->host);
   delete w;
 }
@@ -787,6 +817,7 @@ struct Ctx {
   }
   int mode = 0;  // 0: y - J(dtau . y) (pseudo-time step), 1: J^T (dtau . y) (adjoint)
   int precond = 0;  // mode 0: 0 scales by dtau, 1 solves the radial line preconditioner
+  bool ashift = false;  // mode 1: the shifted operator (D - J^T) P^-1 y of the pseudo-time adjoint
 
   // w->line: dinv, diag, lower, upper (forward: lower, diag, upper in slots 2,
   // 1, 3; adjoint: the transposed lines in slots 0, 1, 5); the Thomas factors
@@ -822,7 +853,8 @@ struct Ctx {
   }
 
   // w_out = J^T (dtau . v) by the hand-written VJP of the residual; on FP32-bulk
-  // grids ut holds the FP32 copy of U and the cotangent goes through rm / rt
+  // grids ut holds the FP32 copy of U and the cotangent goes through rm / rt.
+  // With ashift: w_out = (D - J^T) P^-1 v.
   void adjoint_op(const double* v, double* wout) {
     if (precond == 1) {
       line_solve(v, w->z);
@@ -831,12 +863,20 @@ struct Ctx {
                                                       w->nblk, rows.minr, 0);
       ++launches;
     }
+    vjp(w->z, wout);
+    if (ashift) {
+      shift_combine_kernel<<<grid, NKB, 0, st>>>(wout, w->z, w->dtau, N, n);
+      ++launches;
+    }
+  }
+  // w_out = J^T v (FP64 in and out)
+  void vjp(const double* v, double* wout) {
     int nl = 0;
     cudaError_t e;
     if (g->d.precision == CRN_FP64) {
-      e = launch_vjp_fp64(g, (const double*)w->ut, w->z, wout, nullptr, st, &nl);
+      e = launch_vjp_fp64(g, (const double*)w->ut, v, wout, nullptr, st, &nl);
     } else {
-      perturb_kernel<float><<<grid, NKB, 0, st>>>(w->z, nullptr, nullptr, 0.0, n, (float*)w->rm);
+      perturb_kernel<float><<<grid, NKB, 0, st>>>(v, nullptr, nullptr, 0.0, n, (float*)w->rm);
       ++launches;
       e = launch_vjp_fp32(g, (const float*)w->ut, (const float*)w->rm, (float*)w->rt, nullptr, st, &nl);
       widen_kernel<<<grid, NKB, 0, st>>>((const float*)w->rt, n, wout);
@@ -1171,6 +1211,8 @@ int check_nk_options(const crn_nk_options& o) {
   if (o.fd_central != 0 && o.fd_central != 1) return report(CRN_E_ARG, "fd_central must be 0 or 1");
   if (o.precond != 0 && o.precond != 1) return report(CRN_E_ARG, "precond must be 0 or 1");
   if (o.basis_fp32 < -1 || o.basis_fp32 > 1) return report(CRN_E_ARG, "basis_fp32 must be -1, 0 or 1");
+  if (!(std::isfinite(o.adjoint_cfl) && o.adjoint_cfl >= 0.0)) return report(CRN_E_ARG, "adjoint_cfl must be >= 0");
+  if (o.adjoint_outer < 1 || o.adjoint_outer > 100000) return report(CRN_E_ARG, "adjoint_outer must be in [1, 100000]");
   return CRN_OK;
 }
 
@@ -1194,8 +1236,129 @@ int check_grid(crn_grid* g) {
 
 // adjoint solve J^T lambda = gbar at U (GMRES on J^T diag(dt), lambda = dt . y)
 // and the sensitivity s = -(dR/dB_b)^T lambda
+// (dR/dB_b)^T lambda into sens (negated: the sensitivity -(dR/dB_b)^T lambda),
+// lambda in w->z, the state (or its FP32 copy) in w->ut
+void sensitivity(Ctx& c, double* sens) {
+  crn_grid* g = c.g;
+  NkWork* w = c.w;
+  int nl = 0;
+  cudaError_t e;
+  if (g->d.precision == CRN_FP64) {
+    e = launch_vjp_fp64(g, (const double*)w->ut, w->z, w->w, sens, c.st, &nl);
+  } else {
+    perturb_kernel<float><<<c.grid, NKB, 0, c.st>>>(w->z, nullptr, nullptr, 0.0, c.n, (float*)w->rm);
+    ++c.launches;
+    e = launch_vjp_fp32(g, (const float*)w->ut, (const float*)w->rm, (float*)w->rt, sens, c.st, &nl);
+  }
+  c.launches += nl;
+  ++c.evals;
+  if (c.err == cudaSuccess) c.err = e;
+  const int64_t nb = (int64_t)g->shape.nt * g->shape.np * (g->d.inner_bc == CRN_INNER_LARGE_E ? 2 : 1);
+  scale_kernel<<<(unsigned)((nb + NKB - 1) / NKB), NKB, 0, c.st>>>(sens, sens, -1.0, nb);
+  ++c.launches;
+}
+
+// The adjoint by pseudo-time iteration, the counterpart of the primal's
+// implicit steps: lambda <- lambda + delta with (D - J^T) delta ~= J^T lambda
+// - gbar, D = diag(1 / (adjoint_cfl dt_c)), each correction solved loosely by
+// GMRES (krylov_dim, relative tolerance 1e-2) on the shifted operator, right
+// preconditioned by dtau or by the transposed radial lines of D - J.  The
+// error of lambda contracts by D (D - mu)^-1 per pass for every eigenvalue mu
+// of the (stable) J^T, where GMRES on J^T alone stagnates on large shells.
+// Stops once |gbar - J^T lambda| <= lin_rtol |gbar| or after adjoint_outer
+// passes.
+int adjoint_pseudo_time(crn_grid* g, const double* U, const double* gbar, double* lambda, double* sens,
+                        const crn_nk_options& o, crn_nk_stats* out, cudaStream_t st, int& launches) {
+  cudaError_t e = ensure_work(g, o.krylov_dim);
+  if (e == cudaSuccess && !g->vjp_buf) e = cudaMalloc(&g->vjp_buf, vjp_scratch_bytes(g));
+  if (e == cudaSuccess && !g->nk->adj) e = cudaMalloc(&g->nk->adj, sizeof(double) * 2 * g->nk->n);
+  if (e != cudaSuccess) return report(CRN_E_CUDA, std::string("adjoint workspace: ") + cudaGetErrorString(e));
+  Ctx c(g, st);
+  c.mode = 1;
+  c.precond = o.precond;
+  NkWork* w = c.w;
+  double* lam = w->adj;
+  double* res = w->adj + c.n;
+  if (g->d.precision == CRN_FP64) {
+    local_dt_kernel<double><<<c.grid, NKB, 0, st>>>(g->shape, g->g64.geo, g->d.gamma, g->d.c_h, U,
+                                                    o.adjoint_cfl, w->dtau);
+    cudaMemcpyAsync(w->ut, U, sizeof(double) * c.n, cudaMemcpyDeviceToDevice, st);
+  } else {
+    local_dt_kernel<float><<<c.grid, NKB, 0, st>>>(g->shape, g->g32.geo, g->d.gamma, g->d.c_h, U,
+                                                   o.adjoint_cfl, w->dtau);
+    perturb_kernel<float><<<c.grid, NKB, 0, st>>>(U, nullptr, nullptr, 0.0, c.n, (float*)w->ut);
+    ++c.launches;
+  }
+  ++c.launches;
+  if (o.precond == 1) {  // the radial lines of D - J at this CFL, transposed
+    double* L = w->line;
+    if (g->d.precision == CRN_FP64)
+      line_coef_kernel<double><<<c.grid, NKB, 0, st>>>(g->shape, g->g64.geo, g->d.gamma, g->d.c_h, U,
+                                                       o.adjoint_cfl, L, L + c.N, L + 2 * c.N, L + 3 * c.N);
+    else
+      line_coef_kernel<float><<<c.grid, NKB, 0, st>>>(g->shape, g->g32.geo, g->d.gamma, g->d.c_h, U,
+                                                      o.adjoint_cfl, L, L + c.N, L + 2 * c.N, L + 3 * c.N);
+    line_transpose_kernel<<<c.grid, NKB, 0, st>>>(g->shape, L);  // writes the negated transposed lines
+    negate_kernel<<<c.grid, NKB, 0, st>>>(L, c.N);
+    negate_kernel<<<c.grid, NKB, 0, st>>>(L + 5 * c.N, c.N);
+    c.launches += 4;
+    c.line_factor();
+  }
+  cudaMemsetAsync(lam, 0, sizeof(double) * c.n, st);
+  cudaMemcpyAsync(res, gbar, sizeof(double) * c.n, cudaMemcpyDeviceToDevice, st);
+  const double gnorm = c.norm(res);
+  if (!c.ok()) return report(CRN_E_CUDA, std::string("adjoint solve: ") + cudaGetErrorString(c.err));
+  crn_nk_options inner = o;
+  inner.max_restarts = 0;
+  inner.lin_rtol = 1e-2;
+  int kry = 0, pass = 0;
+  double rel = gnorm > 0.0 ? 1.0 : 0.0;
+  c.ashift = true;
+  for (; pass < o.adjoint_outer && rel > o.lin_rtol; ++pass) {
+    if (pass > 0) {  // res = gbar - J^T lambda
+      c.vjp(lam, w->w);
+      sub_kernel<<<c.grid, NKB, 0, st>>>(res, gbar, w->w, c.n);
+      ++c.launches;
+      rel = c.norm(res) / gnorm;
+      if (!c.ok()) return report(CRN_E_CUDA, std::string("adjoint solve: ") + cudaGetErrorString(c.err));
+      if (!(rel > o.lin_rtol)) break;
+      if (!std::isfinite(rel)) return report(CRN_E_NONPHYSICAL, "the pseudo-time adjoint iteration diverged");
+    }
+    // (D - J^T) delta = -res, delta = P^-1 y
+    scale_kernel<<<c.grid, NKB, 0, st>>>(w->b, res, -1.0, c.n);
+    ++c.launches;
+    int it = 0;
+    gmres(c, U, inner, 0.0, rel * gnorm, it);
+    kry += it;
+    if (o.precond == 1) {
+      c.line_solve(w->x, w->z);
+    } else {
+      precond_kernel<double><<<w->nblk, NKB, 0, st>>>(w->x, w->dtau, c.N, w->z, nullptr, nullptr, 0.0, w->part,
+                                                      w->nblk, c.rows.minr, 0);
+      ++c.launches;
+    }
+    add_kernel<<<c.grid, NKB, 0, st>>>(lam, w->z, c.n);
+    ++c.launches;
+  }
+  c.ashift = false;
+  cudaMemcpyAsync(w->z, lam, sizeof(double) * c.n, cudaMemcpyDeviceToDevice, st);
+  if (lambda) cudaMemcpyAsync(lambda, lam, sizeof(double) * c.n, cudaMemcpyDeviceToDevice, st);
+  if (sens) sensitivity(c, sens);
+  if (!c.ok()) return report(CRN_E_CUDA, std::string("adjoint solve: ") + cudaGetErrorString(c.err));
+  launches += c.launches;
+  if (out) {
+    out->res_l2 = gnorm;
+    out->lin_rel = rel;
+    out->alpha = (double)pass;  // passes of the outer iteration
+    out->krylov_iters = kry;
+    out->residual_evals = c.evals;
+  }
+  return CRN_OK;
+}
+
 int adjoint_solve(crn_grid* g, const double* U, const double* gbar, double* lambda, double* sens,
                   const crn_nk_options& o, crn_nk_stats* out, cudaStream_t st, int& launches) {
+  if (o.adjoint_cfl > 0.0) return adjoint_pseudo_time(g, U, gbar, lambda, sens, o, out, st, launches);
   cudaError_t e = ensure_work(g, o.krylov_dim);
   if (e == cudaSuccess && !g->vjp_buf) e = cudaMalloc(&g->vjp_buf, vjp_scratch_bytes(g));
   if (e != cudaSuccess) return report(CRN_E_CUDA, std::string("adjoint workspace: ") + cudaGetErrorString(e));
@@ -1239,23 +1402,7 @@ int adjoint_solve(crn_grid* g, const double* U, const double* gbar, double* lamb
     ++c.launches;
   }
   if (lambda) cudaMemcpyAsync(lambda, w->z, sizeof(double) * c.n, cudaMemcpyDeviceToDevice, st);
-  if (sens) {
-    // (dR/dB_b)^T lambda from one more VJP, then negated
-    int nl = 0;
-    if (g->d.precision == CRN_FP64) {
-      e = launch_vjp_fp64(g, (const double*)w->ut, w->z, w->w, sens, st, &nl);
-    } else {
-      perturb_kernel<float><<<c.grid, NKB, 0, st>>>(w->z, nullptr, nullptr, 0.0, c.n, (float*)w->rm);
-      ++c.launches;
-      e = launch_vjp_fp32(g, (const float*)w->ut, (const float*)w->rm, (float*)w->rt, sens, st, &nl);
-    }
-    c.launches += nl;
-    ++c.evals;
-    if (c.err == cudaSuccess) c.err = e;
-    const int64_t nb = (int64_t)g->shape.nt * g->shape.np * (g->d.inner_bc == CRN_INNER_LARGE_E ? 2 : 1);
-    scale_kernel<<<(unsigned)((nb + NKB - 1) / NKB), NKB, 0, st>>>(sens, sens, -1.0, nb);
-    ++c.launches;
-  }
+  if (sens) sensitivity(c, sens);  // (dR/dB_b)^T lambda from one more VJP, negated
   if (!c.ok()) return report(CRN_E_CUDA, std::string("adjoint solve: ") + cudaGetErrorString(c.err));
   launches += c.launches;
   if (out) {
@@ -1283,6 +1430,8 @@ int crn_nk_options_default(crn_nk_options* o) {
   o->max_rel_change = 0.3;
   o->fd_central = 1;
   o->basis_fp32 = -1;
+  o->adjoint_outer = 200;
+  o->adjoint_cfl = 0.0;
   return CRN_OK;
 }
 
