@@ -503,37 +503,50 @@ def run_gb300(args):
 
 
 def run_vjp(torch, np, pg, ci, device, stream):
-    """Residual VJP on the 64 x 32 x 64 perturbed shell (adjoint workload),
-    FP64 and FP32 bulk, timed with CUDA events over repeated calls."""
+    """Residual VJP on the 64 x 32 x 64 perturbed shell (adjoint workload) and
+    on the 128 x 64 x 128 benchmark shell, FP64 and FP32 bulk, timed with CUDA
+    events over repeated calls, beside the forward residual on the same grid
+    and state (ratio = VJP time / residual time)."""
     vjp = {}
-    wv = ci.workload("shell64")
-    nv = int(np.prod(wv["shape"]))
-    for precision in ("fp64", "fp32"):
-        gv = pg.Grid(*wv["shape"], precision=precision, p_b=wv["p_b"])
-        gv.set_inner_boundary(torch.from_numpy(wv["Br"]).to(device))
-        dtv = torch.float64 if precision == "fp64" else torch.float32
-        Uv = torch.from_numpy(wv["U"]).to(device, dtv)
-        Rbv = torch.from_numpy(ci.cotangent(wv["U"].shape, seed=4)).to(device, dtv)
-        Ubv = torch.empty_like(Uv)
-        Brbv = torch.empty(wv["shape"][1:], dtype=torch.float64, device=device)
+
+    def timed(fn, nrep):
         with torch.cuda.stream(stream):
             for _ in range(3):
-                gv.residual_vjp(Uv, Rbv, Ubv, Brbv, stream=stream)
+                fn()
         stream.synchronize()
-        nrep = 20 if precision == "fp64" else 50
-        v0 = torch.cuda.Event(enable_timing=True)
-        v1 = torch.cuda.Event(enable_timing=True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
         with torch.cuda.stream(stream):
-            v0.record(stream)
+            e0.record(stream)
             for _ in range(nrep):
-                gv.residual_vjp(Uv, Rbv, Ubv, Brbv, stream=stream)
-            v1.record(stream)
+                fn()
+            e1.record(stream)
         torch.cuda.synchronize(device)
-        ms = v0.elapsed_time(v1) / nrep
-        vjp[precision] = {"ms_per_vjp": ms, "cells_per_s": nv / (ms / 1e3),
-                          "launches_per_vjp": gv.last_launch_count}
-        gv.close()
-    vjp["workload"] = "64x32x64 shell, dipole, 1% perturbation (seed 3), N(0,1) cotangent (seed 4)"
+        return e0.elapsed_time(e1) / nrep
+
+    for name, label in (("shell64", "64x32x64 shell, dipole, 1% perturbation (seed 3)"),
+                        ("shell128", "128x64x128 shell, Parker wind + dipole + l<=15 field (seed 2209)")):
+        wv = ci.workload(name)
+        nv = int(np.prod(wv["shape"]))
+        out = {"workload": label + ", N(0,1) cotangent (seed 4)"}
+        for precision in ("fp64", "fp32"):
+            gv = pg.Grid(*wv["shape"], precision=precision, p_b=wv["p_b"])
+            gv.set_inner_boundary(torch.from_numpy(wv["Br"]).to(device))
+            dtv = torch.float64 if precision == "fp64" else torch.float32
+            Uv = torch.from_numpy(wv["U"]).to(device, dtv)
+            Rbv = torch.from_numpy(ci.cotangent(wv["U"].shape, seed=4)).to(device, dtv)
+            Ubv = torch.empty_like(Uv)
+            Rv = torch.empty_like(Uv)
+            Brbv = torch.empty(wv["shape"][1:], dtype=torch.float64, device=device)
+            nrep = (20 if precision == "fp64" else 50) if name == "shell64" else (5 if precision == "fp64" else 30)
+            ms = timed(lambda: gv.residual_vjp(Uv, Rbv, Ubv, Brbv, stream=stream), nrep)
+            nl = gv.last_launch_count
+            ms_f = timed(lambda: gv.residual(Uv, Rv, stream=stream), nrep)
+            gv.sync_status()
+            out[precision] = {"ms_per_vjp": ms, "cells_per_s": nv / (ms / 1e3), "launches_per_vjp": nl,
+                              "ms_per_residual": ms_f, "vjp_over_residual": ms / ms_f}
+            gv.close()
+        vjp[name] = out
     return vjp
 
 

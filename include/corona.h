@@ -172,10 +172,17 @@ int crn_residual(crn_grid* g, const void* U_dev, void* R_dev, double* norms9_dev
  * Rbar_dev has the layout of R.  Brbar_dev may be NULL; for CRN_INNER_LARGE_E
  * grids it is [2][n_theta][n_phi] (cotangents of B_r and B_theta).  Face states are
  * recomputed, not stored.  Non-smooth points: max passes the derivative to
- * its first argument on a tie, d|x|/dx = +1 at 0.  The first call on a grid
- * allocates its scratch (36 values of the grid's type per face, about 108 per
- * cell): make it before any stream capture.  Asynchronous, 2 launches (3 on
- * CRN_FP64 grids, which recover the primitives once first). */
+ * its first argument on a tie, d|x|/dx = +1 at 0.
+ * CRN_FP32_BULK grids run the tiled VJP: a radial pass over blocks of 16
+ * columns x 13 planes and a lateral pass over 8 x 32 (theta, phi) tiles of
+ * one plane, every intermediate in shared memory; no scratch, 2 launches.
+ * CRN_FP64 grids (and grids created with CRN_KERNEL_CELLWISE) run the
+ * face/cell pair: one thread per face, then one per cell, 3 launches (2 with
+ * FP32), with a scratch of 36 values of the grid's type per face (about 108
+ * per cell) allocated by the grid's first VJP call: make that call before
+ * any stream capture.  The environment variable CRN_VJP_KERNEL ("tiled" or
+ * "faces"), read at each call, overrides the choice.  Ubar_dev must not
+ * overlap U_dev or Rbar_dev (CRN_E_ARG).  Asynchronous. */
 int crn_residual_vjp(crn_grid* g, const void* U_dev, const void* Rbar_dev, void* Ubar_dev,
                      double* Brbar_dev, void* stream);
 

@@ -465,7 +465,7 @@ int crn_residual_vjp(crn_grid* g, const void* U_dev, const void* Rbar_dev, void*
   if (!is_device_ptr(U_dev) || !is_device_ptr(Rbar_dev) || !is_device_ptr(Ubar_dev) ||
       (Brbar_dev && !is_device_ptr(Brbar_dev)))
     return fail(CRN_E_ARG, "VJP arguments must be device pointers");
-  if (!g->vjp_buf) {  // first VJP call of this grid: face-contribution scratch
+  if (!g->vjp_buf && crn::vjp_scratch_bytes(g) > 0) {  // first VJP call: face-contribution scratch
     cudaError_t e = cudaMalloc(&g->vjp_buf, crn::vjp_scratch_bytes(g));
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(VJP scratch)");
   }

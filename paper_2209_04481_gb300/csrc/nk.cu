@@ -1270,7 +1270,8 @@ void sensitivity(Ctx& c, double* sens) {
 int adjoint_pseudo_time(crn_grid* g, const double* U, const double* gbar, double* lambda, double* sens,
                         const crn_nk_options& o, crn_nk_stats* out, cudaStream_t st, int& launches) {
   cudaError_t e = ensure_work(g, o.krylov_dim);
-  if (e == cudaSuccess && !g->vjp_buf) e = cudaMalloc(&g->vjp_buf, vjp_scratch_bytes(g));
+  if (e == cudaSuccess && !g->vjp_buf && vjp_scratch_bytes(g) > 0)
+    e = cudaMalloc(&g->vjp_buf, vjp_scratch_bytes(g));
   if (e == cudaSuccess && !g->nk->adj) e = cudaMalloc(&g->nk->adj, sizeof(double) * 2 * g->nk->n);
   if (e != cudaSuccess) return report(CRN_E_CUDA, std::string("adjoint workspace: ") + cudaGetErrorString(e));
   Ctx c(g, st);
@@ -1360,7 +1361,8 @@ int adjoint_solve(crn_grid* g, const double* U, const double* gbar, double* lamb
                   const crn_nk_options& o, crn_nk_stats* out, cudaStream_t st, int& launches) {
   if (o.adjoint_cfl > 0.0) return adjoint_pseudo_time(g, U, gbar, lambda, sens, o, out, st, launches);
   cudaError_t e = ensure_work(g, o.krylov_dim);
-  if (e == cudaSuccess && !g->vjp_buf) e = cudaMalloc(&g->vjp_buf, vjp_scratch_bytes(g));
+  if (e == cudaSuccess && !g->vjp_buf && vjp_scratch_bytes(g) > 0)
+    e = cudaMalloc(&g->vjp_buf, vjp_scratch_bytes(g));
   if (e != cudaSuccess) return report(CRN_E_CUDA, std::string("adjoint workspace: ") + cudaGetErrorString(e));
   Ctx c(g, st);
   c.mode = 1;

@@ -2,8 +2,11 @@
 // included by vjp_fp64.cu and vjp_fp32.cu.
 #pragma once
 
+#include <cstdlib>
+#include <cstring>
+
 #include "corona_internal.h"
-#include "vjp.cuh"
+#include "vjp_tiled.cuh"
 
 namespace crn {
 
@@ -13,6 +16,22 @@ template <> inline const Geo<float>& vgeo<float>(const crn_grid* g) { return g->
 template <class T> const Phys<T>& vphys(const crn_grid* g);
 template <> inline const Phys<double>& vphys<double>(const crn_grid* g) { return g->ph64; }
 template <> inline const Phys<float>& vphys<float>(const crn_grid* g) { return g->ph32; }
+
+// Which VJP a grid runs.  FP32-bulk grids: the tiled two-pass VJP of
+// vjp_tiled.cuh (issue-bound; its on-chip intermediates replace 864 B/cell of
+// face scratch that would not fit in L2 at production sizes).  FP64 grids:
+// the face/cell pair of vjp.cuh, which evaluates each face exactly once; on
+// the FP64 pipe (1/64 of the FP32 rate) the tiled pass's redundant halo faces
+// cost more than its scratch traffic saves.  Grids created with the
+// cell-wise reference kernel take the face/cell pair too.  CRN_VJP_KERNEL
+// ("tiled" or "faces") overrides the choice.
+inline bool vjp_uses_scratch(const crn_grid* g) {
+  if (const char* e = std::getenv("CRN_VJP_KERNEL")) {
+    if (std::strcmp(e, "tiled") == 0) return false;
+    if (std::strcmp(e, "faces") == 0) return true;
+  }
+  return g->d.kernel == CRN_KERNEL_CELLWISE || g->d.precision == CRN_FP64;
+}
 
 inline size_t vjp_scratch_elems(const Shape& s) {
   const size_t cs = (size_t)s.nt * s.np;
@@ -43,12 +62,50 @@ cudaError_t vjp_lim(crn_grid* g, const T* U, const T* Rb, T* Ub, double* Brb, cu
   return cudaGetLastError();
 }
 
+// Tile of the lateral pass: FP32 8 x 32 (256 threads, two CTAs per SM),
+// FP64 8 x 16 (its shared memory is twice as large per cell).
+template <class T> struct LatTile;
+template <> struct LatTile<float> { static constexpr int TT = 8, TP = 32, MINB = 2; };
+template <> struct LatTile<double> { static constexpr int TT = 8, TP = 16, MINB = 2; };
+
+template <class T, int LIM>
+cudaError_t vjp_tiled_lim(crn_grid* g, const T* U, const T* Rb, T* Ub, double* Brb, cudaStream_t st,
+                          int* nl) {
+  constexpr int TT = LatTile<T>::TT, TP = LatTile<T>::TP;
+  using D = LatDims<TT, TP>;
+  const Shape sh = g->shape;
+  const int64_t cs = (int64_t)sh.nt * sh.np;
+  auto krad = vjp_radial<T, LIM>;
+  auto klat = vjp_lateral<T, LIM, TT, TP, LatTile<T>::MINB>;
+  constexpr size_t smem_rad = radial_smem_bytes<T>();
+  constexpr size_t smem_lat = D::template smem_bytes<T>();
+  static bool attr_set = false;  // per instantiation; the attribute is per device function
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(krad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rad);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(klat, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_lat);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const dim3 grad((unsigned)((cs + RCOL - 1) / RCOL), (unsigned)((sh.nr + RK - 1) / RK));
+  krad<<<grad, RF * RCOL, smem_rad, st>>>(sh, vgeo<T>(g), vphys<T>(g), g->br, U, Rb, Ub, Brb);
+  const int ntiles = ((sh.nt + TT - 1) / TT) * ((sh.np + TP - 1) / TP);
+  klat<<<dim3((unsigned)ntiles, (unsigned)sh.nr), TT * TP, smem_lat, st>>>(sh, vgeo<T>(g), vphys<T>(g), U, Rb,
+                                                                             Ub);
+  *nl = 2;
+  return cudaGetLastError();
+}
+
 template <class T>
 cudaError_t vjp_t(crn_grid* g, const T* U, const T* Rb, T* Ub, double* Brb, cudaStream_t st, int* nl) {
+  const bool ref = vjp_uses_scratch(g);
   switch (g->d.limiter) {
-    case CRN_LIM_NONE: return vjp_lim<T, 0>(g, U, Rb, Ub, Brb, st, nl);
-    case CRN_LIM_MINMOD: return vjp_lim<T, 1>(g, U, Rb, Ub, Brb, st, nl);
-    default: return vjp_lim<T, 2>(g, U, Rb, Ub, Brb, st, nl);
+    case CRN_LIM_NONE:
+      return ref ? vjp_lim<T, 0>(g, U, Rb, Ub, Brb, st, nl) : vjp_tiled_lim<T, 0>(g, U, Rb, Ub, Brb, st, nl);
+    case CRN_LIM_MINMOD:
+      return ref ? vjp_lim<T, 1>(g, U, Rb, Ub, Brb, st, nl) : vjp_tiled_lim<T, 1>(g, U, Rb, Ub, Brb, st, nl);
+    default:
+      return ref ? vjp_lim<T, 2>(g, U, Rb, Ub, Brb, st, nl) : vjp_tiled_lim<T, 2>(g, U, Rb, Ub, Brb, st, nl);
   }
 }
 

@@ -1,0 +1,152 @@
+"""The tiled VJP (vjp_radial + vjp_lateral in vjp_tiled.cuh) on the shapes
+where its tiling has edges: n_theta of 2 and 3 (a tile's 3-cell halo crosses
+a pole twice), n_phi below the tile width, ragged tiles and column groups,
+radial blocks that end at the inner boundary, in the interior and next to the
+outer boundary, every limiter and the boundary variants of Sect. 3.2 /
+Table 2; in FP32 (its default) and FP64 (on request: FP64 grids default to
+the face/cell VJP).
+
+Checked against the oracle's dual-number JVP through the dot-product
+identity <Rbar, J v> = <J^T Rbar, v> (exact up to rounding), and element by
+element against the face/cell VJP of the reference kernels (vjp.cuh), which
+shares only the per-face adjoint arithmetic with it and none of its
+stencil, halo, pole or chunk handling.
+"""
+import numpy as np
+import pytest
+
+import coronal_inputs as ci
+import oracle
+from _util import oracle_grid, problem
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 2e-5}
+# tiled against reference: the same derivatives summed in another order
+ELEM = {"fp64": 1e-11, "fp32": 2e-4}
+
+
+def run(shape, U, Br, Rbar, precision, monkeypatch, limiter="vanalbada", vjp="tiled", **kw):
+    """The VJP through crn_residual_vjp; vjp = "tiled" (vjp_tiled.cuh) or
+    "faces" (the face/cell pair of vjp.cuh), chosen with CRN_VJP_KERNEL."""
+    import paper_2209_04481_gb300 as pg
+    monkeypatch.setenv("CRN_VJP_KERNEL", vjp)
+    g = pg.Grid(*shape, precision=precision, limiter=limiter, p_b=ci.parker_sound_speed2(), **kw)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    g.set_inner_boundary(torch.from_numpy(np.ascontiguousarray(Br)).cuda())
+    Ub, Brb = g.residual_vjp(torch.from_numpy(U).to("cuda", dt), torch.from_numpy(Rbar).to("cuda", dt))
+    g.sync_status()
+    nl = g.last_launch_count
+    out = Ub.double().cpu().numpy(), Brb.cpu().numpy(), nl
+    g.close()
+    monkeypatch.delenv("CRN_VJP_KERNEL", raising=False)
+    return out
+
+
+def dot_identity(og, U, Br, Rbar, Ub, Brb, tol):
+    for seed in (100, 101):
+        r = np.random.default_rng(seed)
+        dU = r.standard_normal(U.shape) * (np.abs(U) + 1e-3)
+        dBr = r.standard_normal(Br.shape)
+        _, Jv = oracle.residual_jvp(og, U, Br, dU, dBr)
+        assert np.all(np.isfinite(Jv))
+        lhs = np.sum(Rbar * Jv)
+        rhs = np.sum(Ub * dU) + np.sum(Brb * dBr)
+        scale = np.sum(np.abs(Rbar * Jv))
+        assert abs(lhs - rhs) <= tol * scale, (seed, lhs, rhs, scale)
+
+
+def elementwise(A, B, tol):
+    A = A.reshape(A.shape[0], -1) if A.ndim > 1 else A[None]
+    B = B.reshape(A.shape)
+    for v in range(A.shape[0]):
+        sc = np.abs(B[v]).max() + 1e-300
+        err = np.abs(A[v] - B[v]).max() / sc
+        assert err <= tol, (v, err)
+
+
+SHAPES = [(2, 2, 8), (3, 3, 8), (5, 4, 16), (7, 10, 40), (12, 17, 48), (16, 8, 64)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("limiter", ["vanalbada", "minmod", "none"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_tiled_vjp_dot_product_identity(shape, limiter, precision, monkeypatch):
+    if limiter == "none" and precision == "fp32":
+        # unlimited radial reconstruction on fewer than ~20 planes over
+        # 1..21.5 R_sun extrapolates to negative face densities and
+        # pressures; the derivative is still defined (and checked in FP64),
+        # but FP32 rounding then decides the sign of the fast-speed
+        # discriminant.  32 planes keep every face state physical.
+        shape = (32,) + tuple(shape[1:])
+    U, Br = problem(shape, perturb=3)
+    Rbar = np.random.default_rng(4).standard_normal(U.shape)
+    Ub, Brb, nl = run(shape, U, Br, Rbar, precision, monkeypatch, limiter)
+    assert nl == 2
+    dot_identity(oracle_grid(shape, limiter=limiter), U, Br, Rbar, Ub, Brb, TOL[precision])
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_tiled_vjp_matches_reference_vjp(shape, precision, monkeypatch):
+    U, Br = problem(shape, perturb=8)
+    Rbar = np.random.default_rng(12).standard_normal(U.shape)
+    Ut, Bt, _ = run(shape, U, Br, Rbar, precision, monkeypatch)
+    Ur, Brr, nl = run(shape, U, Br, Rbar, precision, monkeypatch, vjp="faces")
+    assert nl == (3 if precision == "fp64" else 2)
+    elementwise(Ut, Ur, ELEM[precision])
+    elementwise(Bt, Brr, ELEM[precision])
+
+
+@pytest.mark.parametrize("nr", [12, 13, 14, 15, 26, 27, 40])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_tiled_vjp_radial_blocks(nr, precision, monkeypatch):
+    """The radial pass works on blocks of 13 planes: a block with one plane
+    missing, a whole block, a last block of 1 or 2 planes, of 13 + 13, 13 + 1
+    and 13 + 1 planes (block ends at both boundaries and in the interior);
+    8 x 32 = 256 columns, so that the 16-column groups are whole."""
+    shape = (nr, 8, 32)
+    U, Br = problem(shape, perturb=9)
+    Rbar = np.random.default_rng(5).standard_normal(U.shape)
+    Ut, Bt, _ = run(shape, U, Br, Rbar, precision, monkeypatch)
+    Uf, Bf, _ = run(shape, U, Br, Rbar, precision, monkeypatch, vjp="faces")
+    elementwise(Ut, Uf, ELEM[precision])
+    elementwise(Bt, Bf, ELEM[precision])
+    if nr in (14, 27):
+        dot_identity(oracle_grid(shape), U, Br, Rbar, Ut, Bt, TOL[precision])
+
+
+@pytest.mark.parametrize("variant", ["large_e", "low_e_wp", "case9", "r-2.5", "psi_damp",
+                                     "thin_last+case1", "large_e+case9"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_tiled_vjp_boundary_variants(variant, precision, monkeypatch):
+    from test_gpu_bc_variants import VARIANTS, inputs
+    shape = (10, 12, 24)
+    kw = VARIANTS[variant]
+    U, Br = inputs(shape, variant)
+    Rbar = np.random.default_rng(6).standard_normal(U.shape)
+    Ub, Brb, _ = run(shape, U, Br, Rbar, precision, monkeypatch, **kw)
+    dot_identity(oracle_grid(shape, **kw), U, Br, Rbar, Ub, Brb, TOL[precision])
+    Ur, Brr, _ = run(shape, U, Br, Rbar, precision, monkeypatch, vjp="faces", **kw)
+    elementwise(Ub, Ur, ELEM[precision])
+    elementwise(Brb, Brr, ELEM[precision])
+
+
+def test_tiled_vjp_is_deterministic(monkeypatch):
+    """Fixed-order gathers, no atomics: two calls agree bit for bit."""
+    import paper_2209_04481_gb300 as pg
+    shape = (16, 24, 96)
+    U, Br = problem(shape, perturb=2)
+    Rbar = np.random.default_rng(1).standard_normal(U.shape).astype(np.float32)
+    monkeypatch.delenv("CRN_VJP_KERNEL", raising=False)
+    g = pg.Grid(*shape, precision="fp32", p_b=ci.parker_sound_speed2())
+    g.set_inner_boundary(torch.from_numpy(Br).cuda())
+    Ud = torch.from_numpy(U).to("cuda", torch.float32)
+    Rd = torch.from_numpy(Rbar).cuda()
+    a = [t.cpu().numpy() for t in g.residual_vjp(Ud, Rd)]
+    b = [t.cpu().numpy() for t in g.residual_vjp(Ud, Rd)]
+    g.sync_status()
+    assert g.last_launch_count == 2   # FP32 grids default to the tiled VJP
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    g.close()
