@@ -150,3 +150,54 @@ def test_tiled_vjp_is_deterministic(monkeypatch):
     assert g.last_launch_count == 2   # FP32 grids default to the tiled VJP
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
     g.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_vjp_full_size_128x64x128(precision, monkeypatch):
+    """The benchmark's workload and launch configuration (128 x 64 x 128,
+    Parker wind + dipole + l <= 15 field, N(0, 1) cotangent seed 4; the
+    grid's default VJP: tiled in FP32, face/cell in FP64).
+
+    Dot-product identity against the oracle's JVP.  At this size and field
+    strength the identity is ill-conditioned in FP64: the sum of 9.4 M terms
+    cancels to 1 part in 1300 of its absolute sum, and the fast speed's max
+    and |u_n| sit near their kinks at some faces, so a 1-ulp change of the
+    inputs moves the oracle's own value by ~1e-9 of the absolute sum (more
+    than 1e-12).  The FP64 bar is therefore measured in the test: four times
+    the spread of the oracle's value under two random 1-ulp perturbations of
+    U.  FP32: the 2e-5 bar of the other tests.  Then the tiled and the
+    face/cell VJP element by element (both precisions)."""
+    w = ci.workload("shell128")
+    U, Br = w["U"], w["Br"]
+    shape = U.shape[1:]
+    Rbar = ci.cotangent(U.shape, seed=4)
+    monkeypatch.delenv("CRN_VJP_KERNEL", raising=False)
+    import paper_2209_04481_gb300 as pg
+    g = pg.Grid(*shape, precision=precision, p_b=w["p_b"])
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    g.set_inner_boundary(torch.from_numpy(Br).cuda())
+    Ub, Brb = g.residual_vjp(torch.from_numpy(U).to("cuda", dt), torch.from_numpy(Rbar).to("cuda", dt))
+    g.sync_status()
+    assert g.last_launch_count == (3 if precision == "fp64" else 2)
+    Ub, Brb = Ub.double().cpu().numpy(), Brb.cpu().numpy()
+    g.close()
+    og = oracle_grid(shape, p_b=w["p_b"])
+    if precision == "fp32":
+        dot_identity(og, U, Br, Rbar, Ub, Brb, TOL[precision])
+    else:
+        r = np.random.default_rng(100)
+        dU = r.standard_normal(U.shape) * (np.abs(U) + 1e-3)
+        dBr = r.standard_normal(Br.shape)
+        vals = []
+        for s in (0, 1, 2):
+            Up = U if s == 0 else U * (1 + np.random.default_rng(s).choice([-1.0, 1.0], U.shape) * 2.0 ** -52)
+            _, Jv = oracle.residual_jvp(og, Up, Br, dU, dBr)
+            assert np.all(np.isfinite(Jv))
+            vals.append(np.sum(Rbar * Jv))
+        spread = max(abs(vals[1] - vals[0]), abs(vals[2] - vals[0]))
+        rhs = np.sum(Ub * dU) + np.sum(Brb * dBr)
+        assert abs(vals[0] - rhs) <= 4 * spread, (vals, rhs)
+    other = "faces" if precision == "fp32" else "tiled"
+    Uo, Bo, _ = run(shape, U, Br, Rbar, precision, monkeypatch, vjp=other)
+    elementwise(Ub, Uo, ELEM[precision])
+    elementwise(Brb, Bo, ELEM[precision])
