@@ -165,8 +165,14 @@ def test_vjp_full_size_128x64x128(precision, monkeypatch):
     inputs moves the oracle's own value by ~1e-9 of the absolute sum (more
     than 1e-12).  The FP64 bar is therefore measured in the test: four times
     the spread of the oracle's value under two random 1-ulp perturbations of
-    U.  FP32: the 2e-5 bar of the other tests.  Then the tiled and the
-    face/cell VJP element by element (both precisions)."""
+    U.  FP32: the 2e-5 bar of the other tests.
+
+    Then the tiled and the face/cell VJP element by element, on the same
+    field with the 1 % perturbation of the adjoint workload (seed 3): the
+    unperturbed Parker wind is exactly radial, so V.n of every phi face is
+    zero up to rounding, and where the fast speed sets lambda the sign of
+    that rounding (which differs with the FMA contraction of each kernel)
+    picks the one-sided derivative of |u_n| at about 80 cells."""
     w = ci.workload("shell128")
     U, Br = w["U"], w["Br"]
     shape = U.shape[1:]
@@ -197,7 +203,9 @@ def test_vjp_full_size_128x64x128(precision, monkeypatch):
         spread = max(abs(vals[1] - vals[0]), abs(vals[2] - vals[0]))
         rhs = np.sum(Ub * dU) + np.sum(Brb * dBr)
         assert abs(vals[0] - rhs) <= 4 * spread, (vals, rhs)
-    other = "faces" if precision == "fp32" else "tiled"
-    Uo, Bo, _ = run(shape, U, Br, Rbar, precision, monkeypatch, vjp=other)
-    elementwise(Ub, Uo, ELEM[precision])
-    elementwise(Brb, Bo, ELEM[precision])
+    _, info = ci.background(*shape)
+    Up = ci.perturb(info["W"], seed=3)
+    Ut, Bt, _ = run(shape, Up, Br, Rbar, precision, monkeypatch, vjp="tiled")
+    Uf, Bf, _ = run(shape, Up, Br, Rbar, precision, monkeypatch, vjp="faces")
+    elementwise(Ut, Uf, ELEM[precision])
+    elementwise(Bt, Bf, ELEM[precision])
