@@ -311,7 +311,7 @@ vjp_lateral(Shape sh, Geo<T> g, Phys<T> ph, const T* __restrict__ U, const T* __
   using D = LatDims<TT, TP>;
   constexpr int NT = D::NT, HP = D::HP, HC = D::HT * D::HP, RP = D::RP, RC = D::RT * D::RP;
   constexpr int NFT = D::NFT, NFP = D::NFP;
-  static_assert(2 * TP + 2 * TT <= NT, "one halo cell per thread in the slope pass");
+  static_assert(NT % 32 == 0 && TT >= 2 && TP >= 2, "tile shape");
   extern __shared__ __align__(16) unsigned char lat_smem[];
   T* sW = reinterpret_cast<T*>(lat_smem);   // [NV][HT][HP] primitives
   T* sR = sW + NV * HC;                      // [NV][RT][RP] Rbar / V
@@ -524,6 +524,42 @@ vjp_lateral(Shape sh, Geo<T> g, Phys<T> ph, const T* __restrict__ U, const T* __
       dir[v] = u + l + ab[v] - bb[v];
     }
   };
+  // one variable of it
+  auto slope_adj1 = [&](int v, int wc, int wstep, const T* F, int nf, int fu, int fl, T& ab, T& bb) {
+    const T* p = sW + v * HC + wc;
+    const T wm = p[-wstep], w0 = p[0], wq = p[wstep];
+    T da, db;
+    slope_d<LIM>(w0 - wm, wq - w0, ph.eps, da, db);
+    const T sb = half * (F[v * nf + fu] - F[(NV + v) * nf + fl]);
+    ab = sb * da;
+    bb = sb * db;
+  };
+  // the phi halo columns i0 - 1 and i0 + TP feed columns 0 and TP - 1: their
+  // 2 TT x NV one-variable tasks are spread over the threads, computed now
+  // and stored in the phi pass
+  constexpr int PH = (2 * TT * NV + NT - 1) / NT;
+  T phalo[PH];
+  int phalo_at[PH];   // offset in sX (xlo: [0, NV NT), xhi: [NV NT, 2 NV NT)); -1: none
+#pragma unroll
+  for (int m = 0; m < PH; ++m) {
+    const int t = tid + m * NT;
+    phalo[m] = zero;
+    phalo_at[m] = -1;
+    if (t < 2 * TT * NV) {
+      const int v = t / (2 * TT), h = t % (2 * TT);
+      const int r = h % TT, f0 = r * (TP + 3);
+      T a, b;
+      if (h < TT) {
+        slope_adj1(v, (r + 3) * HP + 2, 1, sFp, NFP, f0 + 1, f0, a, b);
+        phalo[m] = b;
+        phalo_at[m] = v * NT + r * TP;
+      } else {
+        slope_adj1(v, (r + 3) * HP + TP + 3, 1, sFp, NFP, f0 + TP + 2, f0 + TP + 1, a, b);
+        phalo[m] = -a;
+        phalo_at[m] = NV * NT + v * NT + r * TP + TP - 1;
+      }
+    }
+  }
   // theta: own cell (jj, ii) is frame (jj + 3, ii + 3); its upper face is
   // theta face row jj + 2, its lower face row jj + 1
   {
@@ -535,18 +571,20 @@ vjp_lateral(Shape sh, Geo<T> g, Phys<T> ph, const T* __restrict__ U, const T* __
       if (jj + 1 < TT) xlo[v * NT + tid + TP] = bb[v];
       if (jj >= 1) xhi[v * NT + tid - TP] = -ab[v];
     }
-    if (tid < 2 * TP) {  // halo rows: j0 - 1 feeds row 0, j0 + TT feeds row TT - 1
-      // row j0 - 1 (frame row 2) lies between theta face rows 0 and 1, row
-      // j0 + TT (frame row TT + 3) between face rows TT + 1 and TT + 2
-      const int c = tid % TP;
-      const bool lo = tid < TP;
-      T d2[NV], a2[NV], b2v[NV];
-      if (lo) slope_adj(2 * HP + c + 3, HP, sFt, NFT, 1 * TP + c, 0 * TP + c, d2, a2, b2v);
-      else slope_adj((TT + 3) * HP + c + 3, HP, sFt, NFT, (TT + 2) * TP + c, (TT + 1) * TP + c, d2, a2, b2v);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        if (lo) xlo[v * NT + c] = b2v[v];
-        else xhi[v * NT + (TT - 1) * TP + c] = -a2[v];
+    // halo rows j0 - 1 (frame row 2, between theta face rows 0 and 1) and
+    // j0 + TT (frame row TT + 3, between face rows TT + 1 and TT + 2) feed
+    // rows 0 and TT - 1; their 2 TP x NV one-variable tasks are spread over
+    // all threads
+    for (int t = tid; t < 2 * TP * NV; t += NT) {
+      const int v = t / (2 * TP), h = t % (2 * TP);
+      const int c = h % TP;
+      T a, b;
+      if (h < TP) {
+        slope_adj1(v, 2 * HP + c + 3, HP, sFt, NFT, TP + c, c, a, b);
+        xlo[v * NT + c] = b;
+      } else {
+        slope_adj1(v, (TT + 3) * HP + c + 3, HP, sFt, NFT, (TT + 2) * TP + c, (TT + 1) * TP + c, a, b);
+        xhi[v * NT + (TT - 1) * TP + c] = -a;
       }
     }
   }
@@ -565,20 +603,9 @@ vjp_lateral(Shape sh, Geo<T> g, Phys<T> ph, const T* __restrict__ U, const T* __
       if (ii + 1 < TP) xlo[v * NT + tid + 1] = bb[v];
       if (ii >= 1) xhi[v * NT + tid - 1] = -ab[v];
     }
-    if (tid >= 2 * TP && tid < 2 * TP + 2 * TT) {  // halo columns i0 - 1 and i0 + TP
-      const int h = tid - 2 * TP;
-      const int r = h % TT;
-      const bool lo = h < TT;
-      const int f0 = r * (TP + 3);
-      T d2[NV], a2[NV], b2v[NV];
-      if (lo) slope_adj((r + 3) * HP + 2, 1, sFp, NFP, f0 + 1, f0 + 0, d2, a2, b2v);
-      else slope_adj((r + 3) * HP + TP + 3, 1, sFp, NFP, f0 + TP + 2, f0 + TP + 1, d2, a2, b2v);
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        if (lo) xlo[v * NT + r * TP] = b2v[v];
-        else xhi[v * NT + r * TP + TP - 1] = -a2[v];
-      }
-    }
+    for (int m = 0; m < PH; ++m)
+      if (phalo_at[m] >= 0) sX[phalo_at[m]] = phalo[m];
   }
   __syncthreads();
 #pragma unroll
