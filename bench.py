@@ -685,14 +685,15 @@ def run_nk(torch, pg, ci, device, stream, only=None, steps_cap=None):
             reached = a
         g.set_inner_boundary(torch.from_numpy(dip + reached * (Brf - dip)).to(device))
         out["shell96_l15_fp32"] = {
-            "shape": list(shape), "limiter": "minmod", "precision": "fp32 bulk flux, FP64 update and norms",
+            "shape": list(shape), "limiter": "minmod",
+            "precision": "fp32 bulk flux in the Jacobian-vector products; FP64 update, norms and each step's R(U)",
             "magnetogram": "l<=15 random field (seed 2209): B_r = cos(theta) + a s f, max|B_r| = 5 at a = 1",
             "amplitude_reached": reached, "max_abs_br_reached": float(np.abs(dip + reached * (Brf - dip)).max()),
             "continuation": stages, "seconds": total, "stage_tol_drop": 1e-3, "cfl_max": 128.0, "nk_options": nk96,
             "note": "stages stop where the conservative low-beta energy drives a cell's pressure to ~1e-10 of "
                     "B^2 (a finite-difference product then meets a non-physical state); from the last stage a "
-                    "further solve at CFL 128-1024 stalls near a 1e-1 drop of its own start (FP32-bulk "
-                    "residual noise and marginal modes)"}
+                    "further solve at CFL 128-1024 stalls near a 5e-2 to 1e-1 drop of its own start, with or "
+                    "without the FP64 outer residual (oscillating history: slow or limit-cycling modes)"}
         out["shell96_l15_fp32"]["sensitivity"] = _adjoints(torch, ci, g, U64, shape, device, stream, adj_opt)
         g.close()
     return out

@@ -300,6 +300,12 @@ typedef struct {
                               - gbar with D = diag(1 / (adjoint_cfl dt_c)), each pass
                               solved by GMRES(krylov_dim) to 1e-2 on the shifted
                               operator (precond as for the primal lines, transposed)  */
+  int32_t outer_fp64;      /* FP32-bulk grids: 1 (default) evaluates each step's
+                              R(U), the right-hand side and the convergence norm, with
+                              the FP64 residual on the FP64 state, so that the solve
+                              converges past the FP32 rounding of the residual; the
+                              Jacobian-vector products stay FP32-bulk.  0: R(U) in
+                              FP32 bulk too.  Ignored on FP64 grids.                  */
 } crn_nk_options;
 
 typedef struct {

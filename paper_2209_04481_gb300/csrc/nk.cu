@@ -935,16 +935,26 @@ struct Ctx {
   }
 };
 
-// base residual b = R(U) (FP64) and, on FP32 grids, its FP32 copy in rb
-void base_residual(Ctx& c, const double* U) {
+// base residual b = R(U) (FP64) and, on FP32 grids, the FP32-bulk residual
+// of the FP32 copy of U in rb (the base of forward differences); with
+// outer64, b is the FP64 residual of the FP64 state instead of rb widened
+void base_residual(Ctx& c, const double* U, bool outer64) {
   if (c.g->d.precision == CRN_FP64) {
     c.residual(U, c.w->b);
   } else {
     perturb_kernel<float><<<c.grid, NKB, 0, c.st>>>(U, nullptr, nullptr, 0.0, c.n, (float*)c.w->ut);
     ++c.launches;
     c.residual(c.w->ut, c.w->rb);
-    widen_kernel<<<c.grid, NKB, 0, c.st>>>((const float*)c.w->rb, c.n, c.w->b);
-    ++c.launches;
+    if (outer64) {
+      int nl = 0;
+      const cudaError_t e = launch_residual_fp64(c.g, U, c.w->b, nullptr, nullptr, c.st, &nl);
+      c.launches += nl;
+      ++c.evals;
+      if (c.err == cudaSuccess) c.err = e;
+    } else {
+      widen_kernel<<<c.grid, NKB, 0, c.st>>>((const float*)c.w->rb, c.n, c.w->b);
+      ++c.launches;
+    }
   }
 }
 
@@ -1124,7 +1134,16 @@ int nk_step(crn_grid* g, double* U, double cfl, const crn_nk_options& o, crn_nk_
   absmean_kernel<<<w->nblk, NKB, 0, st>>>(U, c.N, w->part, w->nblk, c.rows.sumabs);
   ++c.launches;
   c.finish(c.rows.sumabs, NV, 0);
-  base_residual(c, U);
+  const bool outer64 = g->d.precision == CRN_FP32_BULK && o.outer_fp64 != 0;
+  if (outer64) {  // the FP64 tiled kernels' shared-memory opt-in (an FP32-bulk grid skips it)
+    static bool prepared = false;
+    if (!prepared) {
+      e = prepare_fp64();
+      if (e != cudaSuccess) return report(CRN_E_CUDA, std::string("FP64 residual set-up: ") + cudaGetErrorString(e));
+      prepared = true;
+    }
+  }
+  base_residual(c, U, outer64);
   const double bnorm = c.norm(w->b);
   if (!c.ok()) return report(CRN_E_CUDA, std::string("Newton-Krylov: ") + cudaGetErrorString(c.err));
   int flagged = read_flags(g, st, bad_cell);
@@ -1213,6 +1232,7 @@ int check_nk_options(const crn_nk_options& o) {
   if (o.basis_fp32 < -1 || o.basis_fp32 > 1) return report(CRN_E_ARG, "basis_fp32 must be -1, 0 or 1");
   if (!(std::isfinite(o.adjoint_cfl) && o.adjoint_cfl >= 0.0)) return report(CRN_E_ARG, "adjoint_cfl must be >= 0");
   if (o.adjoint_outer < 1 || o.adjoint_outer > 100000) return report(CRN_E_ARG, "adjoint_outer must be in [1, 100000]");
+  if (o.outer_fp64 != 0 && o.outer_fp64 != 1) return report(CRN_E_ARG, "outer_fp64 must be 0 or 1");
   return CRN_OK;
 }
 
@@ -1434,6 +1454,7 @@ int crn_nk_options_default(crn_nk_options* o) {
   o->basis_fp32 = -1;
   o->adjoint_outer = 200;
   o->adjoint_cfl = 0.0;
+  o->outer_fp64 = 1;
   return CRN_OK;
 }
 

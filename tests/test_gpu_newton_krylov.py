@@ -120,16 +120,32 @@ def test_steady_solve_is_deterministic():
 
 
 def test_steady_solve_fp32_bulk():
-    """FP32-bulk residual inside the solve: the drop is limited by FP32
-    rounding of the residual; 1e-4 is reached and confirmed by the oracle."""
+    """FP32-bulk residual inside the solve (outer_fp64 = 0): the drop is
+    limited by FP32 rounding of the residual; 1e-4 is reached and confirmed
+    by the oracle."""
     shape = (16, 8, 16)
     g, U, Br, og = setup(shape, "large_e", "fp32", dipole_only=True)
     U64 = torch.from_numpy(U).cuda()
-    stats, hist = g.steady_solve(U64, max_steps=300, tol_drop=1e-4)
+    stats, hist = g.steady_solve(U64, max_steps=300, tol_drop=1e-4, nk=dict(outer_fp64=0))
     assert stats["converged"] == 1, (stats, hist[-5:])
     r0 = np.linalg.norm(oracle.residual(og, U, Br)["R"])
     r1 = np.linalg.norm(oracle.residual(og, U64.cpu().numpy(), Br)["R"])
     assert r1 <= 3e-4 * r0
+
+
+def test_steady_solve_fp32_bulk_with_fp64_outer_residual():
+    """The default on FP32-bulk grids: each step's R(U) in FP64 on the FP64
+    state, the Jacobian-vector products in FP32 bulk.  The solve converges
+    past the FP32 rounding floor of the residual to 1e-6, confirmed by the
+    oracle's FP64 residual of the final state."""
+    shape = (16, 8, 16)
+    g, U, Br, og = setup(shape, "large_e", "fp32", dipole_only=True)
+    U64 = torch.from_numpy(U).cuda()
+    stats, hist = g.steady_solve(U64, max_steps=400, tol_drop=1e-6)
+    assert stats["converged"] == 1, (stats, hist[-5:])
+    r0 = np.linalg.norm(oracle.residual(og, U, Br)["R"])
+    r1 = np.linalg.norm(oracle.residual(og, U64.cpu().numpy(), Br)["R"])
+    assert r1 <= 3e-6 * r0, (r1 / r0)
 
 
 def test_strong_field_start_drains_a_cell():
