@@ -298,7 +298,7 @@ typedef struct {
                               diag(dt_c); > 0 runs the pseudo-time adjoint iteration
                               lambda <- lambda + delta, (D - J^T) delta = J^T lambda
                               - gbar with D = diag(1 / (adjoint_cfl dt_c)), each pass
-                              solved by GMRES(krylov_dim) to 1e-2 on the shifted
+                              solved by GMRES(krylov_dim) to 1e-1 on the shifted
                               operator (precond as for the primal lines, transposed)  */
   int32_t outer_fp64;      /* FP32-bulk grids: 1 (default) evaluates each step's
                               R(U), the right-hand side and the convergence norm, with
