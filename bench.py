@@ -600,14 +600,16 @@ def run_nk(torch, pg, ci, device, stream, only=None, steps_cap=None):
     out = {"note": "inner_bc low_e_wp; wall-clock seconds; Krylov basis FP32 (the default at lin_rtol 1e-3); "
                    "adjoint vectors FP64"}
     nk96 = {"precond": 1, "krylov_dim": 60}
-    # pseudo-time adjoint, stopped at a true linear residual of 1e-6: CFL 1000 for
-    # the outer density (165 passes on the dipole state); the outer-B_r functional
-    # meets the near-null induction modes of the static closed-field regions and
-    # only contracts at a small CFL (30: about 900 passes; none at CFL >= 60)
+    # pseudo-time adjoint at CFL 1000, accelerated by flexible GMRES(30) (the
+    # default), stopped at a true linear residual of 1e-6: on the dipole state
+    # about 115 passes for the outer density and 180 for the outer B_r, whose
+    # near-null induction modes (static closed-field regions) the plain
+    # iteration only contracts at CFL 30 in about 900 passes; on FP32-bulk grids
+    # the outer products use the FP64 VJP (outer_fp64, the default)
     adj_opt = {"mean outer rho": dict(krylov_dim=60, lin_rtol=1e-6, precond=1, adjoint_cfl=1000.0,
                                       adjoint_outer=400),
-               "mean outer B_r": dict(krylov_dim=60, lin_rtol=1e-6, precond=1, adjoint_cfl=30.0,
-                                      adjoint_outer=1200)}
+               "mean outer B_r": dict(krylov_dim=60, lin_rtol=1e-6, precond=1, adjoint_cfl=1000.0,
+                                      adjoint_outer=400)}
 
     def solve(g, U64, **kw):
         torch.cuda.synchronize(device)

@@ -305,7 +305,18 @@ typedef struct {
                               the FP64 residual on the FP64 state, so that the solve
                               converges past the FP32 rounding of the residual; the
                               Jacobian-vector products stay FP32-bulk.  0: R(U) in
-                              FP32 bulk too.  Ignored on FP64 grids.                  */
+                              FP32 bulk too.  Likewise in crn_adjoint_solve with
+                              adjoint_fgmres > 0: the outer products J^T z, the true
+                              residual and the sensitivity from the FP64 VJP of the
+                              FP64 state, the passes with the FP32 VJP.  Ignored on
+                              FP64 grids.                                            */
+  int32_t adjoint_fgmres;  /* crn_adjoint_solve with adjoint_cfl > 0: > 0 (default 30)
+                              accelerates the passes by flexible GMRES on J^T lambda =
+                              gbar with restart length min(adjoint_fgmres, krylov_dim),
+                              each pass its right preconditioner (one more vector of
+                              9N doubles per direction, allocated by the first such
+                              call); 0 runs the plain pass iteration.  adjoint_outer
+                              bounds the passes either way.                           */
 } crn_nk_options;
 
 typedef struct {

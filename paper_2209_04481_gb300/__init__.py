@@ -62,7 +62,7 @@ class NkOptions(ctypes.Structure):
                 ("max_rel_change", ctypes.c_double), ("fd_central", ctypes.c_int32),
                 ("precond", ctypes.c_int32), ("basis_fp32", ctypes.c_int32),
                 ("adjoint_outer", ctypes.c_int32), ("adjoint_cfl", ctypes.c_double),
-                ("outer_fp64", ctypes.c_int32)]
+                ("outer_fp64", ctypes.c_int32), ("adjoint_fgmres", ctypes.c_int32)]
 
 
 class NkStats(ctypes.Structure):

@@ -632,6 +632,9 @@ struct NkWork {
   double* coef = nullptr;  // m + 2 coefficients
   double* host = nullptr;  // pinned mirror of out
   double* adj = nullptr;   // 2n: the pseudo-time adjoint's lambda and residual (first use)
+  double* fv = nullptr;    // (mf + 1) n: outer FGMRES basis of the pseudo-time adjoint
+  double* fz = nullptr;    // mf n: its preconditioned directions
+  int mf = 0;
 };
 
 void nk_free(NkWork* w) {
@@ -642,6 +645,7 @@ void nk_free(NkWork* w) {
   cudaFree(w->Vf); cudaFree(w->wf); cudaFree(w->coef32);
   cudaFree(w->part); cudaFree(w->out); cudaFree(w->coef);
   cudaFree(w->adj);
+  cudaFree(w->fv); cudaFree(w->fz);
   cudaFreeHost(w->host);
   delete w;
 }
@@ -740,10 +744,11 @@ struct Ctx {
     if (err == cudaSuccess) err = cudaStreamSynchronize(st);
   }
   // h[t] = <V_t, v> for t < cnt (into out rows 0..cnt-1); with ww also <v, v>
-  void dots(int cnt, const double* v, bool ww) {
+  void dots(int cnt, const double* v, bool ww) { dots_on(w->V, cnt, v, ww); }
+  void dots_on(const double* base, int cnt, const double* v, bool ww) {
     for (int i0 = 0; i0 < cnt || (i0 == 0 && ww); i0 += MD) {
       const int c = std::min(MD, cnt - i0);
-      mdot_kernel<<<w->nblk, NKB, 0, st>>>(w->V, n, i0, std::max(c, 0), v, w->part, w->nblk, i0,
+      mdot_kernel<<<w->nblk, NKB, 0, st>>>(base, n, i0, std::max(c, 0), v, w->part, w->nblk, i0,
                                            (ww && i0 == 0) ? 1 : 0, rows.ww);
       ++launches;
       if (i0 + MD >= cnt) break;
@@ -757,13 +762,14 @@ struct Ctx {
     return std::sqrt(std::max(w->host[rows.ww], 0.0));
   }
   // y += sum_t c[t] V_t
-  void combine(double* y, const double* c, int cnt) {
+  void combine(double* y, const double* c, int cnt) { combine_on(y, w->V, c, cnt); }
+  void combine_on(double* y, const double* base, const double* c, int cnt) {
     if (!ok() || cnt <= 0) return;
     // a copy from pageable memory returns once the source has been staged, so
     // c may be reused at once; stream order keeps coef intact for maxpy
     err = cudaMemcpyAsync(w->coef, c, sizeof(double) * cnt, cudaMemcpyHostToDevice, st);
     if (err != cudaSuccess) return;
-    maxpy_kernel<double><<<grid, NKB, 0, st>>>(y, w->V, n, w->coef, cnt);
+    maxpy_kernel<double><<<grid, NKB, 0, st>>>(y, base, n, w->coef, cnt);
     ++launches;
   }
   // FP32 basis: h[t] = <Vf_t, vf> (rows 0..cnt-1), with ww also <vf, vf>
@@ -1233,6 +1239,7 @@ int check_nk_options(const crn_nk_options& o) {
   if (!(std::isfinite(o.adjoint_cfl) && o.adjoint_cfl >= 0.0)) return report(CRN_E_ARG, "adjoint_cfl must be >= 0");
   if (o.adjoint_outer < 1 || o.adjoint_outer > 100000) return report(CRN_E_ARG, "adjoint_outer must be in [1, 100000]");
   if (o.outer_fp64 != 0 && o.outer_fp64 != 1) return report(CRN_E_ARG, "outer_fp64 must be 0 or 1");
+  if (o.adjoint_fgmres < 0 || o.adjoint_fgmres > 500) return report(CRN_E_ARG, "adjoint_fgmres must be in [0, 500]");
   return CRN_OK;
 }
 
@@ -1276,6 +1283,138 @@ void sensitivity(Ctx& c, double* sens) {
   const int64_t nb = (int64_t)g->shape.nt * g->shape.np * (g->d.inner_bc == CRN_INNER_LARGE_E ? 2 : 1);
   scale_kernel<<<(unsigned)((nb + NKB - 1) / NKB), NKB, 0, c.st>>>(sens, sens, -1.0, nb);
   ++c.launches;
+}
+
+// Krylov acceleration of the pseudo-time adjoint: flexible GMRES(mf) on
+// J^T lambda = gbar, right-preconditioned by one pass of the iteration, z =
+// (J^T - D)^-1 v solved loosely like a pass (so the preconditioner changes from
+// one application to the next: flexible GMRES keeps the directions z_j).  The
+// passes damp the modes with |mu| >> D; the outer minimisation removes the few
+// slow ones that the plain iteration contracts by d / (d - mu) ~ 1 per pass.
+// lam and res (= gbar - J^T lam) on entry and exit; pass counts the
+// preconditioner applications, kry their Krylov steps, rel the final true
+// relative residual.
+int adjoint_fgmres(Ctx& c, const double* U, const double* gbar, double* lam, double* res, double gnorm,
+                   const crn_nk_options& inner, const crn_nk_options& o, int& pass, int& kry, double& rel) {
+  NkWork* w = c.w;
+  // FP32-bulk grids with outer_fp64: the outer products J^T z and the true
+  // residual from the FP64 VJP of the FP64 state (the passes keep the FP32
+  // VJP), so that the iteration converges past the FP32 VJP's rounding
+  const bool outer64 = c.g->d.precision == CRN_FP32_BULK && o.outer_fp64 != 0;
+  auto outer_vjp = [&](const double* v, double* wout) {
+    if (!outer64) {
+      c.vjp(v, wout);
+      return;
+    }
+    int nl = 0;
+    const cudaError_t e = launch_vjp_fp64(c.g, U, v, wout, nullptr, c.st, &nl);
+    c.launches += nl;
+    ++c.evals;
+    if (c.err == cudaSuccess) c.err = e;
+  };
+  const int mf = std::min(o.adjoint_fgmres, o.krylov_dim);
+  if (w->mf < mf) {
+    cudaFree(w->fv);
+    cudaFree(w->fz);
+    w->fv = w->fz = nullptr;
+    w->mf = 0;
+    cudaError_t e = cudaMalloc(&w->fv, sizeof(double) * (size_t)(mf + 1) * c.n);
+    if (e == cudaSuccess) e = cudaMalloc(&w->fz, sizeof(double) * (size_t)mf * c.n);
+    if (e != cudaSuccess) {
+      cudaFree(w->fv);
+      cudaFree(w->fz);
+      w->fv = w->fz = nullptr;
+      return report(CRN_E_CUDA, std::string("adjoint FGMRES basis: ") + cudaGetErrorString(e));
+    }
+    w->mf = mf;
+  }
+  std::vector<double> H((size_t)(mf + 1) * mf), cs(mf), sn(mf), gv(mf + 1), y(mf), h(mf + 1), h2(mf + 1);
+  auto Hat = [&](int i, int j) -> double& { return H[(size_t)i * mf + j]; };
+  for (;;) {
+    // the true residual of the current lambda
+    if (pass > 0 || outer64) {
+      outer_vjp(lam, w->w);
+      sub_kernel<<<c.grid, NKB, 0, c.st>>>(res, gbar, w->w, c.n);
+      ++c.launches;
+    }
+    const double beta = c.norm(res);
+    if (!c.ok()) return report(CRN_E_CUDA, std::string("adjoint solve: ") + cudaGetErrorString(c.err));
+    rel = gnorm > 0.0 ? beta / gnorm : 0.0;
+    if (!std::isfinite(rel)) return report(CRN_E_NONPHYSICAL, "the pseudo-time adjoint iteration diverged");
+    if (!(rel > o.lin_rtol) || pass >= o.adjoint_outer) return CRN_OK;
+    scale_kernel<<<c.grid, NKB, 0, c.st>>>(w->fv, res, 1.0 / beta, c.n);
+    ++c.launches;
+    std::fill(gv.begin(), gv.end(), 0.0);
+    gv[0] = beta;
+    int jdone = 0;
+    for (int j = 0; j < mf && pass < o.adjoint_outer; ++j) {
+      double* vj = w->fv + (size_t)j * c.n;
+      double* zj = w->fz + (size_t)j * c.n;
+      double* vn = w->fv + (size_t)(j + 1) * c.n;
+      // z_j = (J^T - D)^-1 v_j: the pass's loose solve of (D - J^T) z = -v_j (|v_j| = 1)
+      scale_kernel<<<c.grid, NKB, 0, c.st>>>(w->b, vj, -1.0, c.n);
+      ++c.launches;
+      int it = 0;
+      gmres(c, U, inner, 0.0, 1.0, it);
+      kry += it;
+      if (o.precond == 1) {
+        c.line_solve(w->x, zj);
+      } else {
+        precond_kernel<double><<<w->nblk, NKB, 0, c.st>>>(w->x, w->dtau, c.N, zj, nullptr, nullptr, 0.0, w->part,
+                                                          w->nblk, c.rows.minr, 0);
+        ++c.launches;
+      }
+      ++pass;
+      outer_vjp(zj, vn);  // J^T z_j
+      // classical Gram-Schmidt against v_0 .. v_j, repeated once if the norm dropped by > 0.7
+      c.dots_on(w->fv, j + 1, vn, true);
+      c.fetch(0, j + 1);
+      c.fetch(c.rows.ww, 1);
+      if (!c.ok()) return report(CRN_E_CUDA, std::string("adjoint solve: ") + cudaGetErrorString(c.err));
+      const double before = std::sqrt(std::max(w->host[c.rows.ww], 0.0));
+      for (int t = 0; t <= j; ++t) { h[t] = w->host[t]; h2[t] = -h[t]; }
+      c.combine_on(vn, w->fv, h2.data(), j + 1);
+      double after = c.norm(vn);
+      if (after < 0.7 * before) {
+        c.dots_on(w->fv, j + 1, vn, false);
+        c.fetch(0, j + 1);
+        if (!c.ok()) return report(CRN_E_CUDA, std::string("adjoint solve: ") + cudaGetErrorString(c.err));
+        for (int t = 0; t <= j; ++t) { h2[t] = -w->host[t]; h[t] += w->host[t]; }
+        c.combine_on(vn, w->fv, h2.data(), j + 1);
+        after = c.norm(vn);
+      }
+      if (!c.ok()) return report(CRN_E_CUDA, std::string("adjoint solve: ") + cudaGetErrorString(c.err));
+      for (int t = 0; t <= j; ++t) Hat(t, j) = h[t];
+      Hat(j + 1, j) = after;
+      if (after > 0.0) {
+        scale_kernel<<<c.grid, NKB, 0, c.st>>>(vn, vn, 1.0 / after, c.n);
+        ++c.launches;
+      }
+      for (int t = 0; t < j; ++t) {
+        const double a = Hat(t, j), bb = Hat(t + 1, j);
+        Hat(t, j) = cs[t] * a + sn[t] * bb;
+        Hat(t + 1, j) = -sn[t] * a + cs[t] * bb;
+      }
+      const double a = Hat(j, j), bb = Hat(j + 1, j);
+      const double r = std::hypot(a, bb);
+      cs[j] = r > 0.0 ? a / r : 1.0;
+      sn[j] = r > 0.0 ? bb / r : 0.0;
+      Hat(j, j) = r;
+      Hat(j + 1, j) = 0.0;
+      gv[j + 1] = -sn[j] * gv[j];
+      gv[j] = cs[j] * gv[j];
+      jdone = j + 1;
+      if (std::fabs(gv[j + 1]) <= o.lin_rtol * gnorm || !(after > 0.0)) break;
+    }
+    // lambda += sum_t y_t z_t, y = H^-1 g
+    for (int t = jdone - 1; t >= 0; --t) {
+      double sm = gv[t];
+      for (int q = t + 1; q < jdone; ++q) sm -= Hat(t, q) * y[q];
+      y[t] = Hat(t, t) != 0.0 ? sm / Hat(t, t) : 0.0;
+    }
+    c.combine_on(lam, w->fz, y.data(), jdone);
+    if (jdone == 0) return CRN_OK;
+  }
 }
 
 // The adjoint by pseudo-time iteration, the counterpart of the primal's
@@ -1336,7 +1475,11 @@ int adjoint_pseudo_time(crn_grid* g, const double* U, const double* gbar, double
   int kry = 0, pass = 0;
   double rel = gnorm > 0.0 ? 1.0 : 0.0;
   c.ashift = true;
-  for (; pass < o.adjoint_outer && rel > o.lin_rtol; ++pass) {
+  if (o.adjoint_fgmres > 0) {
+    const int rc = adjoint_fgmres(c, U, gbar, lam, res, gnorm, inner, o, pass, kry, rel);
+    if (rc != CRN_OK) return rc;
+  }
+  for (; o.adjoint_fgmres == 0 && pass < o.adjoint_outer && rel > o.lin_rtol; ++pass) {
     if (pass > 0) {  // res = gbar - J^T lambda
       c.vjp(lam, w->w);
       sub_kernel<<<c.grid, NKB, 0, st>>>(res, gbar, w->w, c.n);
@@ -1365,7 +1508,19 @@ int adjoint_pseudo_time(crn_grid* g, const double* U, const double* gbar, double
   c.ashift = false;
   cudaMemcpyAsync(w->z, lam, sizeof(double) * c.n, cudaMemcpyDeviceToDevice, st);
   if (lambda) cudaMemcpyAsync(lambda, lam, sizeof(double) * c.n, cudaMemcpyDeviceToDevice, st);
-  if (sens) sensitivity(c, sens);
+  if (sens && o.adjoint_fgmres > 0 && g->d.precision == CRN_FP32_BULK && o.outer_fp64 != 0) {
+    // -(dR/dB_b)^T lambda from the FP64 VJP of the FP64 state, as the outer products
+    int nl = 0;
+    e = launch_vjp_fp64(g, U, lam, w->w, sens, st, &nl);
+    c.launches += nl;
+    ++c.evals;
+    if (c.err == cudaSuccess) c.err = e;
+    const int64_t nb = (int64_t)g->shape.nt * g->shape.np * (g->d.inner_bc == CRN_INNER_LARGE_E ? 2 : 1);
+    scale_kernel<<<(unsigned)((nb + NKB - 1) / NKB), NKB, 0, st>>>(sens, sens, -1.0, nb);
+    ++c.launches;
+  } else if (sens) {
+    sensitivity(c, sens);
+  }
   if (!c.ok()) return report(CRN_E_CUDA, std::string("adjoint solve: ") + cudaGetErrorString(c.err));
   launches += c.launches;
   if (out) {
@@ -1456,6 +1611,7 @@ int crn_nk_options_default(crn_nk_options* o) {
   o->adjoint_outer = 200;
   o->adjoint_cfl = 0.0;
   o->outer_fp64 = 1;
+  o->adjoint_fgmres = 30;
   return CRN_OK;
 }
 

@@ -98,7 +98,10 @@ cudaError_t vjp_tiled_lim(crn_grid* g, const T* U, const T* Rb, T* Ub, double* B
 
 template <class T>
 cudaError_t vjp_t(crn_grid* g, const T* U, const T* Rb, T* Ub, double* Brb, cudaStream_t st, int* nl) {
-  const bool ref = vjp_uses_scratch(g);
+  // the scratch is sized for the grid's own precision: a VJP in the other
+  // precision (the FP64 outer products of an FP32-bulk grid's adjoint) is tiled
+  const bool own = (sizeof(T) == 8) == (g->d.precision == CRN_FP64);
+  const bool ref = own && vjp_uses_scratch(g);
   switch (g->d.limiter) {
     case CRN_LIM_NONE:
       return ref ? vjp_lim<T, 0>(g, U, Rb, Ub, Brb, st, nl) : vjp_tiled_lim<T, 0>(g, U, Rb, Ub, Brb, st, nl);

@@ -78,10 +78,12 @@ def test_adjoint_lambda_solves_the_transposed_system(precond):
     assert torch.linalg.vector_norm(Ub - gbar) <= 1e-8 * torch.linalg.vector_norm(gbar)
 
 
+@pytest.mark.parametrize("fgmres", [30, 0])
 @pytest.mark.parametrize("precond", [0, 1])
 @pytest.mark.parametrize("bc", ["low_e_wp", "large_e"])
-def test_pseudo_time_adjoint_matches_oracle_tangent(bc, precond):
-    """The pseudo-time adjoint iteration (adjoint_cfl > 0): the same
+def test_pseudo_time_adjoint_matches_oracle_tangent(bc, precond, fgmres):
+    """The pseudo-time adjoint iteration (adjoint_cfl > 0), accelerated by
+    flexible GMRES (adjoint_fgmres = 30, the default) and plain: the same
     sensitivity as the oracle's tangent definition, J^T lambda = gbar checked
     with the GPU VJP, and the iteration's own residual below lin_rtol."""
     shape = (6, 6, 16)
@@ -92,7 +94,7 @@ def test_pseudo_time_adjoint_matches_oracle_tangent(bc, precond):
         gb = torch.from_numpy(gbar).cuda()
         lam = torch.empty_like(U64)
         sens, _, st = g.adjoint_solve(U64, gb, lam=lam, krylov_dim=30, lin_rtol=1e-10, precond=precond,
-                                      adjoint_cfl=100.0, adjoint_outer=400)
+                                      adjoint_cfl=100.0, adjoint_outer=400, adjoint_fgmres=fgmres)
         g.sync_status()
         assert st["lin_rel"] <= 1e-10, st
         Ub, _ = g.residual_vjp(U64, lam)
@@ -103,3 +105,37 @@ def test_pseudo_time_adjoint_matches_oracle_tangent(bc, precond):
             ref = oracle.steady_sensitivity(og, U, Br, gbar, dB, rtol=1e-11)
             got = float(np.sum(s * dB))
             assert abs(got - ref) <= 1e-6 * np.sum(np.abs(s * dB)), (name, got, ref, st)
+
+
+@pytest.mark.parametrize("bc", ["low_e_wp", "large_e"])
+def test_pseudo_time_adjoint_on_fp32_bulk_grid_mixed_precision(bc):
+    """FP32-bulk grid, accelerated pseudo-time adjoint with outer_fp64 = 1
+    (the default): the passes use the FP32 VJP, the outer products, the true
+    residual and the sensitivity the FP64 VJP of the FP64 state, so the solve
+    reaches lin_rtol 1e-10 (far below the FP32 VJP's rounding) and the
+    sensitivity matches the oracle's tangent definition at 1e-6.  lambda is
+    checked with the VJP of an FP64 grid of the same shell."""
+    import paper_2209_04481_gb300 as pg
+    shape = (6, 6, 16)
+    g, U64, Br, og = steady(shape, bc, "fp32")
+    U = U64.cpu().numpy()
+    g64 = pg.Grid(*shape, precision="fp64", p_b=ci.background(*shape)[1]["p_b"], inner_bc=bc, vr_star=VR)
+    g64.set_inner_boundary(torch.from_numpy(Br).cuda())
+    rng = np.random.default_rng(13)
+    for name, gbar in objectives(shape, U).items():
+        gb = torch.from_numpy(gbar).cuda()
+        lam = torch.empty_like(U64)
+        sens, _, st = g.adjoint_solve(U64, gb, lam=lam, krylov_dim=30, lin_rtol=1e-10, precond=1,
+                                      adjoint_cfl=100.0, adjoint_outer=400)
+        g.sync_status()
+        assert st["lin_rel"] <= 1e-10, st
+        Ub, _ = g64.residual_vjp(U64, lam)
+        g64.sync_status()
+        assert torch.linalg.vector_norm(Ub - gb) <= 1e-9 * torch.linalg.vector_norm(gb)
+        s = sens.cpu().numpy()
+        for _ in range(2):
+            dB = rng.standard_normal(Br.shape)
+            ref = oracle.steady_sensitivity(og, U, Br, gbar, dB, rtol=1e-11)
+            got = float(np.sum(s * dB))
+            assert abs(got - ref) <= 1e-6 * np.sum(np.abs(s * dB)), (name, got, ref, st)
+    g64.close()

@@ -66,8 +66,8 @@ def test_newton_krylov_option_defaults(lib):
     n = pg.NkOptions()
     assert lib.crn_nk_options_default(ctypes.byref(n)) == 0
     assert n.krylov_dim == 30 and n.lin_rtol == 1e-3
-    assert (n.adjoint_outer, n.adjoint_cfl, n.outer_fp64) == (200, 0.0, 1)
-    assert (o.nk.adjoint_outer, o.nk.adjoint_cfl, o.nk.outer_fp64) == (200, 0.0, 1)
+    assert (n.adjoint_outer, n.adjoint_cfl, n.outer_fp64, n.adjoint_fgmres) == (200, 0.0, 1, 30)
+    assert (o.nk.adjoint_outer, o.nk.adjoint_cfl, o.nk.outer_fp64, o.nk.adjoint_fgmres) == (200, 0.0, 1, 30)
     assert lib.crn_newton_krylov_step(None, None, 2.0, None, None, None, None) == 1
     assert lib.crn_steady_solve(None, None, None, None, None, 0, None) == 1
 
