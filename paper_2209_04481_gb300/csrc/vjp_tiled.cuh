@@ -15,22 +15,27 @@
 //     Wbar_{c-1} -= im_c abar_c,      Wbar_{c+1} += ip_c bbar_c.
 // Every term reaching a cell comes from the faces at most 3/2 cells away.
 //
-//   vjp_radial   one thread per (column, radial chunk): marches outwards
-//                through the r faces of its chunk (and the three beyond its
-//                ends that reach its planes), carrying the last planes'
-//                primitives, cotangents and lower-value cotangents in
-//                registers; the ghosts' cotangents go through the ghost
-//                adjoints (inner: also into Brbar).  Writes the r part of
-//                Wbar into Ubar.
+//   vjp_radial   one CTA per block of 16 columns x 13 planes: the
+//                primitives of planes k0 - 3 .. k0 + 15 (ghost planes built
+//                by the forward ghost maps) and Rbar / V in shared memory;
+//                one thread per r face k0 - 1 .. k0 + 14 (the faces that
+//                reach the block's planes), then one per plane for its slope
+//                adjoint, then one per own plane gathering its neighbours'
+//                terms in a fixed order; the ghosts' cotangents go through
+//                the ghost adjoints (inner: also into Brbar).  Writes the r
+//                part of Wbar into Ubar.
 //   vjp_lateral  one CTA per (theta, phi) tile of one plane: the primitives
 //                of the tile and a 3-cell cross halo (theta arm: the tile's
 //                columns, phi arm: its rows) and Rbar / V with a 2-cell halo
-//                in shared memory; every theta and phi face that reaches a
-//                tile cell gets its adjoint once (face-value cotangents in
-//                shared memory); each cell then takes its slope adjoints and
-//                the neighbours' terms are gathered in a fixed order (no
-//                atomics); the r part is added, then the adjoints of the
-//                primitive recovery and of the sources, in place in Ubar.
+//                in shared memory; each cell's limited slope once, as the
+//                face values of its faces; every theta and phi face that
+//                reaches a tile cell gets its adjoint once, its cotangents
+//                replacing its states; each cell then takes its slope
+//                adjoints and the neighbours' terms are gathered in a fixed
+//                order (no atomics); the r part is added, then the adjoints
+//                of the primitive recovery and of the sources, in place in
+//                Ubar.
+//   Every load of a thread is issued before the first is used.
 //
 // Cells beyond a pole are the cells of the opposite column (Cartesian vector
 // components need no change); a theta face beyond a pole is that column's
