@@ -1142,12 +1142,8 @@ int nk_step(crn_grid* g, double* U, double cfl, const crn_nk_options& o, crn_nk_
   c.finish(c.rows.sumabs, NV, 0);
   const bool outer64 = g->d.precision == CRN_FP32_BULK && o.outer_fp64 != 0;
   if (outer64) {  // the FP64 tiled kernels' shared-memory opt-in (an FP32-bulk grid skips it)
-    static bool prepared = false;
-    if (!prepared) {
-      e = prepare_fp64();
-      if (e != cudaSuccess) return report(CRN_E_CUDA, std::string("FP64 residual set-up: ") + cudaGetErrorString(e));
-      prepared = true;
-    }
+    e = prepare_fp64();
+    if (e != cudaSuccess) return report(CRN_E_CUDA, std::string("FP64 residual set-up: ") + cudaGetErrorString(e));
   }
   base_residual(c, U, outer64);
   const double bnorm = c.norm(w->b);

@@ -79,13 +79,17 @@ cudaError_t vjp_tiled_lim(crn_grid* g, const T* U, const T* Rb, T* Ub, double* B
   auto klat = vjp_lateral<T, LIM, TT, TP, LatTile<T>::MINB>;
   constexpr size_t smem_rad = radial_smem_bytes<T>();
   constexpr size_t smem_lat = D::template smem_bytes<T>();
-  static bool attr_set = false;  // per instantiation; the attribute is per device function
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(krad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rad);
+  // the shared-memory opt-in, once per instantiation and device
+  static bool attr_set[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+    e = cudaFuncSetAttribute(krad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rad);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(klat, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_lat);
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    if (dev >= 0 && dev < 64) attr_set[dev] = true;
   }
   const dim3 grad((unsigned)((cs + RCOL - 1) / RCOL), (unsigned)((sh.nr + RK - 1) / RK));
   krad<<<grad, RF * RCOL, smem_rad, st>>>(sh, vgeo<T>(g), vphys<T>(g), g->br, U, Rb, Ub, Brb);
