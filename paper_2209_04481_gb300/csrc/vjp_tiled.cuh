@@ -320,8 +320,8 @@ vjp_lateral(Shape sh, Geo<T> g, Phys<T> ph, const T* __restrict__ U, const T* __
   extern __shared__ __align__(16) unsigned char lat_smem[];
   T* sW = reinterpret_cast<T*>(lat_smem);   // [NV][HT][HP] primitives
   T* sR = sW + NV * HC;                      // [NV][RT][RP] Rbar / V
-  T* sFt = sR + NV * RC;                     // [2][NV][NFT] theta faces: L, R value cotangents
-  T* sFp = sFt + 2 * NV * NFT;               // [2][NV][NFP] phi faces
+  T* sFt = sR + NV * RC;                     // [2][NV][NFT] theta faces: L, R states, then their cotangents
+  T* sFp = sFt + 2 * NV * NFT;               // [2][NV][NFP] phi faces, likewise
   T* sX = sFp + 2 * NV * NFP;                // [2][NV][NT]  neighbour terms (from below, from above)
 
   const int nr = sh.nr, nt = sh.nt, np = sh.np;
